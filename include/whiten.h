@@ -1,0 +1,187 @@
+/*
+ * whiten.h -- C ABI of the B300 clutter-whitening preprocessor.
+ *
+ * Method: H. L. Kennedy, "Parallel software implementation of recursive
+ * multidimensional digital filters for point-target detection in cluttered
+ * infrared scenes" (arXiv:1408.3526).  For every pixel of a frame stream the
+ * library
+ *   (a) updates a local 3-D spectrum recursively: a deadbeat observer bank
+ *       over time and a sliding DFT (comb + resonator) over the M x M spatial
+ *       window (Sec. 1; Eq. (6)-(7));
+ *   (b) forms the high-passed, Hann-windowed power spectrum, its 3-D
+ *       autocorrelation on the lz = 1 slice, smooths it over time and takes
+ *       the background velocity as its peak (Sec. 2; Eq. (9)-(10));
+ *   (c) applies the velocity-tuned frequency-sampling prediction-error
+ *       filter and subtracts the predicted background (Eq. (1)-(5), (8)).
+ *
+ * Conventions (all calls):
+ *   - Frames are float32 intensities, row-major [frame_h][frame_w]; x is the
+ *     column (fast) axis, y the row axis.  A positive velocity moves content
+ *     toward +x / +y by that many pixels per frame.
+ *   - Reads outside the frame clamp to the edge pixel, so every pixel has an
+ *     output; history before the first frame is zero.
+ *   - The caller owns every buffer passed in; the library owns the device
+ *     state and tables it allocates in wh_create_stream and frees in
+ *     wh_destroy_stream.  Nothing is retained after a call returns except
+ *     through the stream object.
+ *   - Every call returns 0 (WH_OK) or a negative WH_E* status; nothing
+ *     aborts and no C++ exception crosses this boundary.
+ *   - Work is enqueued on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  wh_push_frame is asynchronous; the wh_read_*
+ *     calls with a host destination synchronise that stream before returning,
+ *     with a device destination they only enqueue a device-to-device copy.
+ *   - Pointers flagged is_device = 1 must be device pointers on the stream's
+ *     device; is_device = 0 means pageable or pinned host memory.
+ *   - A stream object must not be used from two threads at once.
+ */
+#ifndef WHITEN_H
+#define WHITEN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define WH_OK         0
+#define WH_EINVAL    -1   /* bad argument: even or < 3 window, Mz < 2, grid step <= 0, h or w < 1, NULL */
+#define WH_ENOMEM    -2   /* device or host allocation failed */
+#define WH_EADMIT    -3   /* request exceeds the memory budget (serving admission) */
+#define WH_ENOTREADY -4   /* output not available yet (fewer than m'_z + 1 frames pushed) */
+#define WH_ECUDA     -5   /* a CUDA runtime call failed; the message is in wh_last_error() */
+#define WH_ETIMEOUT  -6   /* a bounded device-side wait ran out (error flag set, no hang) */
+#define WH_EUNSUP    -7   /* parameter combination not built into this library */
+
+/* ---- velocity-estimation and precision modes ---------------------------- */
+#define WH_VEL_PLAIN        0  /* autocorrelation search (Eq. (10)), FP32-exact argmax */
+#define WH_PREC_FP32        0  /* plain form: FP32 recursion, FP32-exact autocorrelation */
+#define WH_PREC_TC_FP16     1  /* autocorrelation contraction on tcgen05, FP16 x FP16 -> FP32 */
+#define WH_PREC_TC_BF16     2  /* autocorrelation contraction on tcgen05, BF16 x BF16 -> FP32 */
+#define WH_PREC_KAHAN       4  /* flag: compensated FP32 sums in the spatial SDFT recursion */
+
+/* Velocity grid: {-vmax, -vmax + step, ..., +vmax} on both axes
+ * (Sec. 3: l_x = l_y = [-8 .. 8]/4, a 17 x 17 grid at vmax = 2, step 1/4).
+ * vmax must be an integer multiple of step; L = 2 vmax/step + 1 <= 33. */
+typedef struct {
+    float vmax;
+    float step;
+} wh_vgrid;
+
+/* Optional parameters; a field left at its "default" value takes the
+ * default shown.  Pass NULL to take every default. */
+typedef struct {
+    int    band;        /* B, PEF spatial half-bandwidth (Eq. (2), W = 2B+1); <= 0: round(M/3) */
+    int    delay_z;     /* m'_z, output delay in frames; < 0: floor((Mz-1)/2) */
+    double alpha;       /* smoother pole (Sec. 2 after Eq. (10)); < 0: exp(-1/10) */
+    int    precision;   /* WH_PREC_* (bit-or WH_PREC_KAHAN) */
+    int    debug_dump;  /* 1: keep the windowed spectrum and power of the last frame for
+                           wh_read_spectrum (slow; tests only) */
+} wh_params;
+
+typedef struct wh_stream wh_stream;   /* opaque */
+
+/* Fill *p with the defaults for a window M and order Mz. */
+int wh_default_params(int window, int temporal_order, wh_params *p);
+
+/*
+ * Create a stream: allocate its device state (observer bank, smoothed
+ * autocorrelation basis, outputs) and build its tables (SDFT twiddles, Hann
+ * taps, Eq. (8)/(2) filter weights per grid velocity, Eq. (10) basis).
+ *   frame_h, frame_w   frame size (>= 1 each)
+ *   window             spatial window M = 2K+1 (odd, 3..15)
+ *   temporal_order     Mz, temporal bins / observer states (2..8)
+ *   velocity_grid      search grid for the autocorrelation peak
+ *   opt                NULL or optional parameters
+ *   cuda_stream        a cudaStream_t (NULL = default stream); not owned
+ *   out                receives the stream handle
+ * Errors: WH_EINVAL, WH_EUNSUP, WH_ENOMEM, WH_ECUDA.
+ */
+int wh_create_stream(int frame_h, int frame_w, int window, int temporal_order,
+                     wh_vgrid velocity_grid, const wh_params *opt, void *cuda_stream,
+                     wh_stream **out);
+
+/*
+ * Push one frame (float32 [h][w]); runs the whole per-pixel path for it:
+ * observer + spatial SDFT + high-pass + Hann + power + smoothing, the
+ * autocorrelation search, and the prediction-error filter.  Asynchronous on
+ * the stream's CUDA stream; a host frame is copied first (the copy is done
+ * before the call returns only if the memory is pageable).
+ * Errors: WH_EINVAL (NULL), WH_ECUDA.
+ */
+int wh_push_frame(wh_stream *s, const float *frame, int is_device);
+
+/*
+ * Whitened (prediction-error) frame E for frame index t - m'_z, where t is
+ * the index of the last frame pushed (first frame = 0), written to
+ * out[h][w].  *frame_index (may be NULL) receives t - m'_z.
+ * Errors: WH_ENOTREADY before m'_z + 1 frames, WH_EINVAL, WH_ECUDA.
+ */
+int wh_read_whitened(wh_stream *s, float *out, int is_device, long long *frame_index);
+
+/*
+ * Background velocity estimate of the last frame pushed, in pixels/frame:
+ * vx[h][w], vy[h][w] (either may be NULL).  vidx (may be NULL) receives the
+ * flat grid index iy*L + ix (int32 [h][w]) with vx = -vmax + ix*step.
+ * *frame_index receives t.  Errors: WH_ENOTREADY before the first frame.
+ */
+int wh_read_velocity(wh_stream *s, float *vx, float *vy, int *vidx, int is_device,
+                     long long *frame_index);
+
+/* Spectrum kinds for wh_read_spectrum. */
+#define WH_SPEC_RAW       0  /* S(k; n) of Eq. (6)-(7), from the observer state */
+#define WH_SPEC_WINDOWED  1  /* high-passed, Hann-windowed spectrum (needs debug_dump) */
+#define WH_SPEC_POWER     2  /* P(k; n) of Eq. (9) (needs debug_dump; real, float32) */
+
+/*
+ * Per-pixel spectrum of the last frame pushed, layout [h][w][Mz][M][M] with
+ * bins kz = -((Mz-1)/2) .. Mz/2, ky, kx = -K .. K (slowest to fastest);
+ * complex64 interleaved (re, im) for RAW and WINDOWED, float32 for POWER.
+ * Errors: WH_ENOTREADY, WH_EINVAL (kind needs debug_dump), WH_ECUDA.
+ */
+int wh_read_spectrum(wh_stream *s, int kind, void *out, int is_device);
+
+/*
+ * Smoothed autocorrelation R'(l; n) of the last frame on the velocity grid,
+ * float32 [h][w][L][L] (ly slowest), recomputed from the stream's smoothed
+ * spectral state (Sec. 2: R is linear in P).  For tests and diagnostics.
+ */
+int wh_read_autocorr(wh_stream *s, float *out, int is_device);
+
+/* Grid length L and the output delay m'_z of a stream. */
+int wh_stream_info(const wh_stream *s, int *grid_len, int *delay_z, int *band,
+                   long long *frames_pushed);
+
+/* Device pointers of the stream's output buffers (valid until destroy):
+ * whitened[h][w], vx[h][w], vy[h][w] (float32), vidx[h][w] (int32).
+ * Any argument may be NULL.  Lets a device consumer read outputs in place. */
+int wh_output_pointers(wh_stream *s, float **whitened, float **vx, float **vy, int **vidx);
+
+/*
+ * Per-kernel timing for measurement: when enabled, wh_push_frame records CUDA
+ * events on the stream around each of its kernels (spectrum, autocorrelation
+ * search, prediction-error filter).  wh_profile_read synchronises the stream
+ * and returns, per kernel, the summed device time in ms (ms[3]) and the number
+ * of timed launches (n[3]); reset = 1 clears the accumulators.  At most 65536
+ * frames are kept between reads; later frames are not timed.
+ */
+int wh_profile_enable(wh_stream *s, int on);
+int wh_profile_read(wh_stream *s, double *ms, long long *n, int reset);
+
+/* Reset the recursive state to zero (as if no frame had been pushed). */
+int wh_reset_stream(wh_stream *s);
+
+/* Free everything the stream owns.  NULL is accepted (no-op). */
+int wh_destroy_stream(wh_stream *s);
+
+/* Human-readable text of a status code (static storage). */
+const char *wh_status_string(int status);
+
+/* Text of the last CUDA error seen on this thread (static per thread). */
+const char *wh_last_error(void);
+
+/* Number of this library's kernels launched since load (all streams). */
+long long wh_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WHITEN_H */

@@ -71,7 +71,8 @@ def _load():
                                     C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
-                                    C.c_void_p, C.c_void_p, C.c_int]
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int]
             _lib = lib
     return _lib
 
@@ -157,14 +158,15 @@ class Oracle:
         return -self.vmax + self.vstep * np.arange(self.L)
 
     def run(self, frames: np.ndarray, crop=None, *, whitened=True, velocity=True,
-            spec_frames=(), spectrum=False, power=False, autocorr=False,
+            spec_frames=(), spectrum=False, power=False, autocorr=False, windowed=False,
             vel_override: np.ndarray | None = None, fixed_v=None, nthreads: int = 0):
         """Run over frames [T][H][W] (float32) for the crop (y0, x0, h, w).
 
         Returns a dict with 'whitened' [T][h][w] (E of frame t - m'z at t,
         NaN before), 'vel_index' [T][h][w], and at ``spec_frames``:
         'spectrum' complex [n][h][w][Mz][M][M], 'power' likewise (real),
-        'autocorr' [n][h][w][L][L] (smoothed R').
+        'autocorr' [n][h][w][L][L] (smoothed R'), 'windowed' complex like
+        'spectrum' (high-passed, Hann-windowed).
         """
         frames = np.ascontiguousarray(frames, np.float32)
         T, H, W = frames.shape
@@ -184,9 +186,11 @@ class Oracle:
         sim = np.zeros((n, h, w, self.nb)) if (spectrum and n) else None
         pw = np.zeros((n, h, w, self.nb)) if (power and n) else None
         rs = np.zeros((n, h, w, self.L * self.L)) if (autocorr and n) else None
+        wre = np.zeros((n, h, w, self.nb)) if (windowed and n) else None
+        wim = np.zeros((n, h, w, self.nb)) if (windowed and n) else None
         rc = self.lib.orc_run(self._h, frames, T, H, W, y0, x0, h, w, _ptr(wh), _ptr(vi),
                               _ptr(vo), _ptr(fv), _ptr(st), n, _ptr(sre), _ptr(sim), _ptr(pw),
-                              _ptr(rs), int(nthreads))
+                              _ptr(rs), _ptr(wre), _ptr(wim), int(nthreads))
         if rc != 0:
             raise RuntimeError(f"oracle run failed ({rc})")
         shp = (n, h, w, self.Mz, self.M, self.M)
@@ -198,6 +202,8 @@ class Oracle:
             out["spectrum"] = (sre + 1j * sim).reshape(shp)
         if pw is not None:
             out["power"] = pw.reshape(shp)
+        if wre is not None:
+            out["windowed"] = (wre + 1j * wim).reshape(shp)
         if rs is not None:
             out["autocorr"] = rs.reshape(n, h, w, self.L, self.L)
         return out

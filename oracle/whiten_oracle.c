@@ -297,6 +297,7 @@ static void hann_line(cplx *v, int n, int lo, int stride, cplx *tmp)
  *   fixed_v[2]              if given, the PEF uses this (vx, vy) everywhere
  *   spec_re/im [nspec][h][w][nb]   S(k; n) at frames spec_t[]
  *   pow_out [nspec][h][w][nb]      P(k; n) at frames spec_t[]
+ *   specw_re/im [nspec][h][w][nb]  high-passed, Hann-windowed spectrum at spec_t[]
  *   rs_out  [nspec][h][w][L*L]     R'(l; n) at frames spec_t[]
  */
 int orc_run(const orc_ctx *c, const float *frames, int T, int H, int W,
@@ -304,7 +305,8 @@ int orc_run(const orc_ctx *c, const float *frames, int T, int H, int W,
             double *whitened, int *vel_index, const int *vel_override,
             const double *fixed_v,
             const int *spec_t, int nspec, double *spec_re, double *spec_im,
-            double *pow_out, double *rs_out, int nthreads)
+            double *pow_out, double *rs_out, double *specw_re, double *specw_im,
+            int nthreads)
 {
     const int M = c->M, K = c->K, Mz = c->Mz, kzlo = c->kzlo, L = c->L;
     const int nb = c->nb, nbp = c->nbp, B = c->B, WB = 2 * B + 1;
@@ -453,6 +455,8 @@ int orc_run(const orc_ctx *c, const float *frames, int T, int H, int W,
                         if (spec_re) spec_re[so + b] = creal(S[b]);
                         if (spec_im) spec_im[so + b] = cimag(S[b]);
                         if (pow_out) pow_out[so + b] = P[b];
+                        if (specw_re) specw_re[so + b] = creal(Sp[b]);
+                        if (specw_im) specw_im[so + b] = cimag(Sp[b]);
                     }
                     if (rs_out)
                         memcpy(rs_out + ((size_t)spec_slot * h * w + pix) * L * L, rs,

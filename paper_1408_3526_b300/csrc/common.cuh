@@ -1,0 +1,101 @@
+// Device-side definitions shared by the whitening kernels (sm_103a).
+//
+// Data layout in HBM (one stream, frame H x W, window M = 2K+1, Mz bins):
+//   obs[2]  [Mz][H][W] f32   observer a-posteriori state T_t(kz), Hermitian
+//                            packed: f=0 Re T(0); f=2j-1,2j Re/Im T(j),
+//                            j=1..J; f=Mz-1 Re T(Mz/2) if Mz even.  Ping-pong:
+//                            the spectrum kernel reads one, writes the other.
+//   Astate  [H*W][kpad] f32  smoothed autocorrelation basis A'(h): index 0 =
+//                            A_c(0,0); 1..nh = A_c(h); nh+1..2nh = A_s(h),
+//                            h over the half plane (kx=0, ky=1..K; then kx=1..K,
+//                            ky=-K..K).  R(l) is a fixed linear map of it.
+//   whitened, vx, vy [H][W] f32; vidx [H][W] i32.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wh {
+
+constexpr int kMaxM = 15;
+constexpr int kMaxMz = 8;
+constexpr int kMaxL = 33;
+constexpr int kMaxPlanes = kMaxMz / 2 + 1;
+constexpr int kMaxChan = 2 * (kMaxM) + (kMaxPlanes) * kMaxM + kMaxPlanes;
+
+// Tables of the spectrum kernel, built on the host in double precision.
+struct SpecTables {
+  int nch;                      // channels incl. the per-plane box-sum (DC) channels
+  int nchy;                     // channels that run the y-SDFT (first nchy)
+  int nplanes;                  // stored temporal planes p = 0..nplanes-1
+  int nh;                       // (M*M-1)/2
+  int nslot;                    // P-gather slots per h: 1 + 2J + even
+  int ch_plane[kMaxChan];
+  int ch_kx[kMaxChan];          // kx of the channel (0 for DC channels)
+  float2 xcoef[kMaxChan][kMaxM];  // x-DFT weights: Hann(mx) e^{j2pi kx (mx-K)/M}; DC: 1
+  float2 wres[kMaxM];           // resonator twiddle e^{+j2pi ky/M}, index ky+K
+  float2 cphase[kMaxM];         // centring phase e^{-j2pi ky K/M}
+  float2 lam[kMaxPlanes];       // observer rotation e^{+j2pi p/Mz}
+  float2 hann_z;                // e^{-j2pi Dz/Mz}
+  float cz[kMaxPlanes], sz[kMaxPlanes];   // cos/sin(2pi p/Mz)
+  float2 uncenter[kMaxM];       // e^{+j2pi k K/M} (debug dump only)
+};
+
+struct SpecArgs {
+  int H, W;
+  int M, Mz;
+  int tw, th;                   // output tile
+  int kpad;
+  float alpha;
+  const float* frame;
+  const float* obs_old;
+  float* obs_new;
+  float* Astate;
+  const SpecTables* tables;     // device copy
+  const int* hgather;           // [nh+1][nslot] offsets (c*M + iy) into a pixel's P block
+  float2* dump_win;             // optional [H*W][Mz][M][M]
+  float* dump_pow;              // optional [H*W][Mz][M][M]
+};
+
+struct AutocorrArgs {
+  int H, W, M, L, kpad;
+  float vmax, vstep;
+  const float* Astate;
+  int* vidx;
+  float* vx;
+  float* vy;
+  float* rs_out;                // optional [H*W][L*L]
+  const float2* tab_y;          // e^{j2pi ky ly/M}: [L][M]   (index ky+K)
+  const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
+};
+
+struct PefArgs {
+  int H, W, M, Mz, L, mpz;
+  const float* obs;             // T_t, just written
+  const int* vidx;
+  const float* hw;              // [L][Mz][M] separable FIR weights (Eq. (2)), incl. scale
+  float* whitened;
+};
+
+struct RawSpecArgs {
+  int H, W, M, Mz;
+  const float* obs;
+  float2* out;                  // [H*W][Mz][M][M]
+};
+
+// complex helpers
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st);
+cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st);
+cudaError_t launch_pef(const PefArgs& a, cudaStream_t st);
+cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
+bool spectrum_supported(int M, int Mz);
+
+}  // namespace wh

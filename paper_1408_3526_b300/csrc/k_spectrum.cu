@@ -1,0 +1,357 @@
+// Spectrum kernel: observer bank + spatial SDFT + high-pass + Hann + power +
+// reduction to the autocorrelation basis + first-order smoothing, fused.
+//
+// Method (Kennedy, arXiv:1408.3526, Sec. 1-2):
+//   S(k;n) = 1/sqrt(Mx My Mz) sum_m e^{j2pi k.m/M} I(n-m)          Eq. (6)-(7)
+// estimated recursively: a deadbeat observer over time and a sliding DFT
+// (comb + resonator) over space.  The observer bank is linear and
+// time-invariant with the same coefficients for every input, so it is run
+// per raw pixel (Mz states) before the spatial SDFT instead of per spatial
+// bin after it; the result is identical and the state is M^2 times smaller.
+// Then the high-passed (kx = ky = 0 removed), Hann-windowed spectrum S'' gives
+// P = |S''|^2 (Eq. (9)) and, summing over kz with the lz = 1 phase,
+//   A_c(h) = sum_kz P(h,kz) cos(2pi kz/Mz),  A_s(h) = sum_kz P(h,kz) sin(2pi kz/Mz)
+// from which R(l) = A_c(0) + 2 sum_{h in half plane} [A_c(h) cos a_h(l) -
+// A_s(h) sin a_h(l)] exactly (Eq. (10), a_h(l) = 2pi(hx lx + hy ly)/M).  The
+// smoother R'_t = (1-alpha) R_t + alpha R'_{t-1} is linear, so it is applied
+// to the M^2 numbers A instead of the L^2 values of R (identical result).
+//
+// Organisation: one CTA owns a strip of TW output columns x TH output rows and
+// walks down it one input row at a time (TH + 2K rows, clamped at the frame
+// edge):
+//   A  observer update of the row segment (TW + 2K pixels), Hann along kz;
+//   B  x-DFT of the row: every (channel, column) as a direct M-tap sum with the
+//      Hann(x) window and the centring phase folded into its weights;
+//   C  y-SDFT: one thread per (channel, column) carries the M ky-resonators
+//      of that column (comb input from a ring of the last M+1 x-DFT rows),
+//      then Hann along ky (real 3 taps in the centred basis), the high-pass
+//      correction and the power of the output row;
+//   D  per output pixel, reduce P over kz into A, smooth, store.
+// Register prefetch hides the HBM latency of the next row's frame/observer
+// state (phase A) and of the next output row's smoother state (phase D).
+#include "common.cuh"
+
+namespace wh {
+
+namespace {
+
+constexpr int kPrefA = kMaxMz + 1;   // frame + Mz state floats per phase-A pixel
+constexpr int kMaxDTasks = 4;        // phase-D tasks per thread (checked on the host)
+constexpr int kSpecMaxThreads = 768;
+
+template <int M, int MZ>
+struct Geo {
+  static constexpr int K = (M - 1) / 2;
+  static constexpr int J = (MZ - 1) / 2;                 // complex planes 1..J
+  static constexpr bool EVEN = (MZ % 2) == 0;
+  static constexpr int NPL = J + 1 + (EVEN ? 1 : 0);     // stored planes
+};
+
+__device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
+
+// Byte offsets of the shared-memory arrays (16-byte aligned each); the same
+// function sizes the launch on the host.
+struct SpecSmem {
+  size_t twr, ring, xc, pbuf, hg, wres, cph, total;
+};
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
+  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
+  const bool even = (Mz % 2) == 0;
+  const int npl = J + 1 + (even ? 1 : 0);
+  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
+  const int nch = nchy + npl;
+  const int nh = (M * M - 1) / 2;
+  const int nslot = 1 + 2 * J + (even ? 1 : 0);
+  const int PS = (nchy * M) | 1;
+  const int RW = tw + 2 * K;
+  SpecSmem L;
+  size_t o = 0;
+  L.twr = o;  o = align16(o + sizeof(float2) * size_t(npl) * RW);
+  L.ring = o; o = align16(o + sizeof(float2) * size_t(M + 1) * nch * tw);
+  L.xc = o;   o = align16(o + sizeof(float2) * size_t(nch) * M);
+  L.pbuf = o; o = align16(o + sizeof(float) * size_t(tw) * PS);
+  L.hg = o;   o = align16(o + sizeof(int) * size_t(nh + 1) * nslot);
+  L.wres = o; o = align16(o + sizeof(float2) * M);
+  L.cph = o;  o = align16(o + sizeof(float2) * M);
+  L.total = o;
+  return L;
+}
+
+template <int M, int MZ>
+__global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const SpecArgs a) {
+  using G = Geo<M, MZ>;
+  constexpr int K = G::K, J = G::J, NPL = G::NPL;
+  constexpr bool EVEN = G::EVEN;
+  const SpecTables& tb = *a.tables;
+  const int TW = a.tw, TH = a.th, H = a.H, W = a.W;
+  const int RW = TW + 2 * K;
+  const int nch = tb.nch, nchy = tb.nchy, nh = tb.nh, nslot = tb.nslot;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int PS = (nchy * M) | 1;                          // odd pixel stride of pbuf
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SpecSmem SL = spec_smem_layout(M, MZ, TW);
+  float2* twr = reinterpret_cast<float2*>(smem_raw + SL.twr);         // [NPL][RW]
+  float2* ring = reinterpret_cast<float2*>(smem_raw + SL.ring);       // [M+1][nch][TW]
+  float2* xc = reinterpret_cast<float2*>(smem_raw + SL.xc);           // [nch][M]
+  float* pbuf = reinterpret_cast<float*>(smem_raw + SL.pbuf);         // [TW][PS]
+  int* hg = reinterpret_cast<int*>(smem_raw + SL.hg);                 // [(nh+1)][nslot]
+  float2* wres = reinterpret_cast<float2*>(smem_raw + SL.wres);       // [M]
+  float2* cph = reinterpret_cast<float2*>(smem_raw + SL.cph);         // [M]
+
+  for (int i = tid; i < nch * M; i += nthr) xc[i] = tb.xcoef[i / M][i % M];
+  for (int i = tid; i < (nh + 1) * nslot; i += nthr) hg[i] = a.hgather[i];
+  for (int i = tid; i < M; i += nthr) { wres[i] = tb.wres[i]; cph[i] = tb.cphase[i]; }
+  float2 lam[NPL];
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) lam[p] = tb.lam[p];
+
+  const float2 hz = tb.hann_z;
+  const float invMz = 1.0f / MZ;
+  const float alpha = a.alpha, oma = 1.0f - alpha;
+  const float sP = float(MZ) * float(MZ) / float(M * M * MZ);   // (Mz/sqrt(N))^2
+
+  // ---- phase-C ownership: one (channel, column) per thread --------------------
+  const bool yth = tid < TW * nchy;
+  const int cy = yth ? tid / TW : 0;
+  const int xy = yth ? tid % TW : 0;
+  const int kxc = tb.ch_kx[cy];
+  const int plc = tb.ch_plane[cy];
+  const int dcch = nchy + plc;                           // this plane's box-sum channel
+  float2 Y[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) Y[k] = make_float2(0.f, 0.f);
+
+  // ---- phase-A prefetch (row i = 0) --------------------------------------------
+  float pa[kPrefA];
+  auto loadA = [&](int i) {
+    if (tid < RW) {
+      const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + tid, W);
+      const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
+      pa[0] = __ldg(a.frame + o);
+#pragma unroll
+      for (int f = 0; f < MZ; ++f) pa[1 + f] = __ldg(a.obs_old + f * plane + o);
+    }
+  };
+  loadA(0);
+
+  // ---- phase-D prefetch (first output row y0) ----------------------------------
+  const int ntD = TW * (nh + 1);
+  float pdc[kMaxDTasks], pds[kMaxDTasks];
+  auto loadD = [&](int yo) {
+#pragma unroll
+    for (int q = 0; q < kMaxDTasks; ++q) {
+      const int task = tid + q * nthr;
+      pdc[q] = 0.f; pds[q] = 0.f;
+      if (task < ntD && yo < H) {
+        const int x = task / (nh + 1), hi = task % (nh + 1);
+        if (x0 + x < W) {
+          const float* src = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
+          pdc[q] = src[hi];
+          if (hi > 0) pds[q] = src[nh + hi];
+        }
+      }
+    }
+  };
+  loadD(y0);
+  __syncthreads();
+
+  const int nrows = TH + 2 * K;
+  for (int i = 0; i < nrows; ++i) {
+    const int r = y0 - K + i;               // input row (unclamped)
+    // ---------------- A: observer update + Hann along kz ---------------------
+    if (tid < RW) {
+      const float xin = pa[0];
+      float2 T[NPL];
+      T[0] = make_float2(pa[1], 0.f);
+#pragma unroll
+      for (int j = 1; j <= J; ++j) T[j] = make_float2(pa[2 * j - 1 + 1], pa[2 * j + 1]);
+      if (EVEN) T[NPL - 1] = make_float2(pa[MZ], 0.f);
+      // prior s = lambda T_{t-1}; prediction = sum over all Mz bins (Hermitian)
+      float2 s[NPL];
+      float yhat = 0.f;
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        s[p] = cmul(lam[p], T[p]);
+        const bool real = (p == 0) || (EVEN && p == NPL - 1);
+        yhat += real ? s[p].x : 2.f * s[p].x;
+      }
+      const float e = (xin - yhat) * invMz;
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        T[p] = make_float2(s[p].x + e, s[p].y);
+        const bool real = (p == 0) || (EVEN && p == NPL - 1);
+        if (real) T[p].y = 0.f;
+      }
+      // owner writes the new state
+      const int xs = x0 - K + tid;
+      if (r >= y0 && r < y0 + TH && r < H && tid >= K && tid < K + TW && xs < W) {
+        const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
+        a.obs_new[o] = T[0].x;
+#pragma unroll
+        for (int j = 1; j <= J; ++j) {
+          a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
+          a.obs_new[(2 * j) * plane + o] = T[j].y;
+        }
+        if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
+      }
+      // Hann along kz: Tw(p) = 1/2 T(p) + 1/4 hz T(p+1) + 1/4 conj(hz) T(p-1), mod Mz
+      float2 Tf[MZ];
+      Tf[0] = T[0];
+#pragma unroll
+      for (int j = 1; j <= J; ++j) { Tf[j] = T[j]; Tf[MZ - j] = conjf2(T[j]); }
+      if (EVEN) Tf[MZ / 2] = T[NPL - 1];
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        const float2 up = Tf[(p + 1) % MZ], dn = Tf[(p + MZ - 1) % MZ];
+        float2 tw = cadd(cscale(Tf[p], 0.5f),
+                         cadd(cscale(cmul(hz, up), 0.25f), cscale(cmul(conjf2(hz), dn), 0.25f)));
+        const bool real = (p == 0) || (EVEN && p == NPL - 1);
+        if (real) tw.y = 0.f;
+        twr[p * RW + tid] = tw;
+      }
+    }
+    if (i + 1 < nrows) loadA(i + 1);
+    __syncthreads();
+
+    // ---------------- B: x-DFT of the row into the ring ---------------------
+    const int slot = i % (M + 1);
+    for (int task = tid; task < nch * TW; task += nthr) {
+      const int c = task / TW, x = task % TW;
+      const int p = tb.ch_plane[c];
+      const float2* row = twr + p * RW + x + 2 * K;     // u = x + 2K - mx
+      const float2* w = xc + c * M;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int mx = 0; mx < M; ++mx) {
+        const float2 v = row[-mx], cw = w[mx];
+        acc.x = fmaf(cw.x, v.x, fmaf(-cw.y, v.y, acc.x));
+        acc.y = fmaf(cw.x, v.y, fmaf(cw.y, v.x, acc.y));
+      }
+      ring[(slot * nch + c) * TW + x] = acc;
+    }
+    __syncthreads();
+
+    // ---------------- C: y-SDFT, Hann(ky), high-pass, power -------------------
+    const int yo = r - K;                    // output row of this window
+    const bool outrow = (i >= 2 * K) && (yo < H);
+    if (yth) {
+      const float2 xn = ring[(slot * nch + cy) * TW + xy];
+      float2 d = xn;
+      if (i >= M) d = csub(xn, ring[(((i - M) % (M + 1)) * nch + cy) * TW + xy]);
+#pragma unroll
+      for (int k = 0; k < M; ++k) Y[k] = cadd(cmul(wres[k], Y[k]), cmul(cph[k], d));
+      if (outrow) {
+        // Hann along ky (real taps 1/4, 1/2, 1/4 in the centred basis), minus
+        // Hann_x Hann_y of the removed (0,0) bin, then the power.
+        float2 D = make_float2(0.f, 0.f);
+        float wxh = 0.f;
+        if (kxc >= -1 && kxc <= 1) {
+#pragma unroll
+          for (int my = 0; my < M; ++my) D = cadd(D, ring[((((i - my) % (M + 1)) * nch) + dcch) * TW + xy]);
+          wxh = (kxc == 0) ? 0.5f : 0.25f;
+        }
+        float* pb = pbuf + xy * PS + cy * M;
+        const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          float2 z = cadd(cscale(Y[k], 0.5f), cscale(cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]), 0.25f));
+          if (k == K) z = csub(z, cscale(D, wxh * 0.5f));
+          if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh * 0.25f));
+          const float pw = sP * fmaf(z.x, z.x, z.y * z.y);
+          pb[k] = pw;
+          if (dump) {
+            // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
+            const size_t pix = size_t(yo) * W + x0 + xy;
+            const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
+            const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
+                                     float(MZ) / sqrtf(float(M * M * MZ)));
+            const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
+            const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
+            a.dump_win[op] = sv;
+            a.dump_win[om] = conjf2(sv);
+            if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- D: reduce over kz, smooth, store -----------------------
+    if (outrow) {
+#pragma unroll
+      for (int q = 0; q < kMaxDTasks; ++q) {
+        const int task = tid + q * nthr;
+        if (task >= ntD) break;
+        const int x = task / (nh + 1), hi = task % (nh + 1);
+        if (x0 + x >= W) continue;
+        const int* g = hg + hi * nslot;
+        const float* pb = pbuf + x * PS;
+        float Ac = pb[g[0]], As = 0.f;
+#pragma unroll
+        for (int j = 1; j <= J; ++j) {
+          const float pp = pb[g[j]], pm = pb[g[J + j]];
+          Ac = fmaf(pp + pm, tb.cz[j], Ac);
+          As = fmaf(pp - pm, tb.sz[j], As);
+        }
+        if (EVEN) Ac -= pb[g[2 * J + 1]];
+        float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
+        dst[hi] = fmaf(oma, Ac, alpha * pdc[q]);
+        if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * pds[q]);
+      }
+      loadD(yo + 1);
+    }
+    // pbuf and the ring slot are rewritten only after the next two barriers
+  }
+}
+
+}  // namespace
+
+// Shared-memory bytes and block size for a configuration (host side).
+struct SpecLaunch { int threads; size_t smem; };
+
+static SpecLaunch spec_launch_shape(int M, int Mz, int tw) {
+  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
+  const bool even = (Mz % 2) == 0;
+  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
+  int threads = ((tw * nchy + 31) / 32) * 32;
+  return {threads, spec_smem_layout(M, Mz, tw).total};
+}
+
+template <int M, int MZ>
+static cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
+  SpecLaunch L = spec_launch_shape(M, MZ, a.tw);
+  auto kern = spectrum_kernel<M, MZ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.W + a.tw - 1) / a.tw, (a.H + a.th - 1) / a.th);
+  kern<<<grid, L.threads, L.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define WH_SPEC_CASES(X) \
+  X(5, 3) X(5, 4) X(5, 5) X(5, 6) \
+  X(7, 3) X(7, 4) X(7, 5) X(7, 6) \
+  X(9, 3) X(9, 4) X(9, 5) X(9, 6) \
+  X(15, 4) X(15, 5) X(15, 6)
+
+bool spectrum_supported(int M, int Mz) {
+#define X(m, z) if (M == m && Mz == z) return true;
+  WH_SPEC_CASES(X)
+#undef X
+  return false;
+}
+
+int spectrum_threads(int M, int Mz, int tw) { return spec_launch_shape(M, Mz, tw).threads; }
+size_t spectrum_smem(int M, int Mz, int tw) { return spec_launch_shape(M, Mz, tw).smem; }
+
+cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st) {
+#define X(m, z) if (a.M == m && a.Mz == z) return launch_spec_t<m, z>(a, st);
+  WH_SPEC_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace wh

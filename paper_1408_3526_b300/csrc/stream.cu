@@ -1,0 +1,499 @@
+// Host runtime of the whitening stream and the C ABI declared in whiten.h.
+//
+// Owns the per-stream device state (observer bank, smoothed autocorrelation
+// basis, outputs), builds the tables in double precision on the host, and
+// enqueues the three kernels of one frame on the stream's CUDA stream:
+//   spectrum (observer + SDFT + high-pass + Hann + power + A reduction + smoothing)
+//   autocorrelation on the velocity grid + argmax
+//   prediction-error filter + subtraction.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/whiten.h"
+#include "common.cuh"
+
+namespace wh {
+int spectrum_threads(int M, int Mz, int tw);
+size_t spectrum_smem(int M, int Mz, int tw);
+}  // namespace wh
+
+using namespace wh;
+
+static std::atomic<long long> g_launches{0};
+static thread_local char g_err[512] = "";
+
+static int set_cuda_err(cudaError_t e, const char* what) {
+  std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+  return WH_ECUDA;
+}
+#define WH_CU(call)                                   \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return set_cuda_err(e__, #call); \
+  } while (0)
+
+static const double kPi = 3.14159265358979323846;
+
+struct wh_stream {
+  int H, W, M, K, Mz, B, mpz, L, precision, debug;
+  double alpha, vmax, vstep;
+  int tw, th, kpad;
+  int device;
+  cudaStream_t st;
+  long long t;          // frames pushed
+  int cur;              // observer buffer holding T_{t-1}
+  float* obs[2];
+  float* Astate;
+  float* frame;
+  float* whitened;
+  float* vx;
+  float* vy;
+  int* vidx;
+  SpecTables* d_spec;
+  int* d_hgather;
+  float2* d_taby;
+  float2* d_tabx;
+  float* d_hw;
+  float2* d_dump_win;
+  float* d_dump_pow;
+  float2* d_raw;
+  float* d_rs;
+  // per-kernel timing (wh_profile_enable)
+  int prof;
+  std::vector<cudaEvent_t> ev;   // 4 per timed frame
+  size_t ev_used;
+};
+
+// ---------------------------------------------------------------------------
+static double dirichlet(int Wd, double w) {   // Eq. (3), limit value at integers
+  double j = std::nearbyint(w), d = w - j;
+  long long ji = (long long)j;
+  double sgn = ((ji * (Wd - 1)) % 2 == 0) ? 1.0 : -1.0;
+  if (std::fabs(d) < 1e-12) return sgn;
+  return sgn * std::sin(kPi * Wd * d) / (Wd * std::sin(kPi * d));
+}
+
+static float2 cexpf2(double ph) { return make_float2(float(std::cos(ph)), float(std::sin(ph))); }
+
+static void build_spec_tables(const wh_stream* s, SpecTables& tb, std::vector<int>& hg) {
+  std::memset(&tb, 0, sizeof(tb));
+  const int M = s->M, K = s->K, Mz = s->Mz;
+  const int J = (Mz - 1) / 2;
+  const bool even = (Mz % 2) == 0;
+  const int npl = J + 1 + (even ? 1 : 0);
+  tb.nplanes = npl;
+  tb.nh = (M * M - 1) / 2;
+  tb.nslot = 1 + 2 * J + (even ? 1 : 0);
+  std::vector<int> base(npl);
+  int c = 0;
+  auto hann = [&](int m) { return 0.5 + 0.5 * std::cos(2.0 * kPi * (m - K) / M); };
+  for (int p = 0; p < npl; ++p) {
+    const bool real = (p == 0) || (even && p == npl - 1);
+    base[p] = c;
+    const int klo = real ? 0 : -K;
+    for (int kx = klo; kx <= K; ++kx, ++c) {
+      tb.ch_plane[c] = p;
+      tb.ch_kx[c] = kx;
+      for (int mx = 0; mx < M; ++mx) {
+        // centred, Hann-windowed x-DFT weight
+        const double ph = 2.0 * kPi * kx * (mx - K) / M;
+        tb.xcoef[c][mx] = make_float2(float(hann(mx) * std::cos(ph)), float(hann(mx) * std::sin(ph)));
+      }
+    }
+  }
+  tb.nchy = c;
+  for (int p = 0; p < npl; ++p, ++c) {   // box-sum channels for the high-pass correction
+    tb.ch_plane[c] = p;
+    tb.ch_kx[c] = 0;
+    for (int mx = 0; mx < M; ++mx) tb.xcoef[c][mx] = make_float2(1.f, 0.f);
+  }
+  tb.nch = c;
+  for (int i = 0; i < M; ++i) {
+    const int k = i - K;
+    tb.wres[i] = cexpf2(2.0 * kPi * k / M);
+    tb.cphase[i] = cexpf2(-2.0 * kPi * k * K / M);
+    tb.uncenter[i] = cexpf2(2.0 * kPi * k * K / M);
+  }
+  for (int p = 0; p < npl; ++p) {
+    const int kz = p;   // the Nyquist plane p = Mz/2 rotates by e^{j pi} = -1
+    tb.lam[p] = cexpf2(2.0 * kPi * kz / Mz);
+    tb.cz[p] = float(std::cos(2.0 * kPi * kz / Mz));
+    tb.sz[p] = float(std::sin(2.0 * kPi * kz / Mz));
+  }
+  tb.hann_z = cexpf2(-2.0 * kPi * ((Mz - 1) / 2.0) / Mz);
+  // gather offsets (c*M + iy) of P for every h in {0} + half plane
+  auto chan = [&](int p, int kx) {
+    const bool real = (p == 0) || (even && p == npl - 1);
+    return base[p] + (real ? kx : kx + K);
+  };
+  const int nslot = tb.nslot;
+  hg.assign(size_t(tb.nh + 1) * nslot, 0);
+  auto fill = [&](int hi, int hx, int hy) {
+    int* g = &hg[size_t(hi) * nslot];
+    g[0] = chan(0, hx) * M + (hy + K);
+    for (int j = 1; j <= J; ++j) {
+      g[j] = chan(j, hx) * M + (hy + K);
+      g[J + j] = chan(j, -hx) * M + (-hy + K);
+    }
+    if (even) g[2 * J + 1] = chan(npl - 1, hx) * M + (hy + K);
+  };
+  fill(0, 0, 0);
+  int hi = 1;
+  for (int ky = 1; ky <= K; ++ky) fill(hi++, 0, ky);
+  for (int kx = 1; kx <= K; ++kx)
+    for (int ky = -K; ky <= K; ++ky) fill(hi++, kx, ky);
+}
+
+static int pick_tile_w(int M, int Mz) {
+  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
+  const bool even = (Mz % 2) == 0;
+  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
+  int tw = 768 / nchy;
+  if (tw > 32) tw = 32;
+  if (tw < 1) tw = 1;
+  return tw;
+}
+
+static void free_stream(wh_stream* s) {
+  if (!s) return;
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
+                  s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
+                  s->d_dump_pow, s->d_raw, s->d_rs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int wh_default_params(int window, int temporal_order, wh_params* p) {
+  if (!p || window < 3 || (window % 2) == 0 || temporal_order < 2) return WH_EINVAL;
+  p->band = int(std::lround(window / 3.0));
+  if (p->band < 1) p->band = 1;
+  p->delay_z = (temporal_order - 1) / 2;
+  p->alpha = std::exp(-0.1);
+  p->precision = WH_PREC_FP32;
+  p->debug_dump = 0;
+  return WH_OK;
+}
+
+int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params* opt,
+                     void* cuda_stream, wh_stream** out) {
+  if (!out) return WH_EINVAL;
+  *out = nullptr;
+  if (H < 1 || W < 1 || M < 3 || (M % 2) == 0 || M > kMaxM || Mz < 2 || Mz > kMaxMz) return WH_EINVAL;
+  if (!(grid.step > 0.f) || !(grid.vmax >= 0.f)) return WH_EINVAL;
+  const double Ld = 2.0 * grid.vmax / grid.step + 1.0;
+  const int L = int(std::lround(Ld));
+  if (std::fabs(Ld - L) > 1e-4 || L < 1 || L > kMaxL) return WH_EINVAL;
+  wh_params p;
+  wh_default_params(M, Mz, &p);
+  if (opt) {
+    if (opt->band > 0) p.band = opt->band;
+    if (opt->delay_z >= 0) p.delay_z = opt->delay_z;
+    if (opt->alpha >= 0) p.alpha = opt->alpha;
+    p.precision = opt->precision;
+    p.debug_dump = opt->debug_dump;
+  }
+  const int K = (M - 1) / 2;
+  if (p.band > K || p.delay_z >= Mz || p.alpha >= 1.0) return WH_EINVAL;
+  if (!spectrum_supported(M, Mz)) return WH_EUNSUP;
+  if ((p.precision & ~WH_PREC_KAHAN) != WH_PREC_FP32) return WH_EUNSUP;
+
+  wh_stream* s = new (std::nothrow) wh_stream();
+  if (!s) return WH_ENOMEM;
+  s->obs[0] = s->obs[1] = nullptr;
+  s->Astate = s->frame = s->whitened = s->vx = s->vy = nullptr;
+  s->vidx = nullptr; s->d_spec = nullptr; s->d_hgather = nullptr; s->d_taby = nullptr;
+  s->d_tabx = nullptr; s->d_hw = nullptr; s->d_dump_win = nullptr; s->d_dump_pow = nullptr;
+  s->d_raw = nullptr; s->d_rs = nullptr; s->prof = 0; s->ev_used = 0; s->t = 0; s->cur = 0;
+  s->H = H; s->W = W; s->M = M; s->K = K; s->Mz = Mz; s->B = p.band; s->mpz = p.delay_z;
+  s->L = L; s->precision = p.precision; s->debug = p.debug_dump;
+  s->alpha = p.alpha; s->vmax = grid.vmax; s->vstep = grid.step;
+  s->st = (cudaStream_t)cuda_stream;
+  s->tw = pick_tile_w(M, Mz);
+  s->th = 64;
+  s->kpad = ((M * M) + 3) & ~3;
+  cudaGetDevice(&s->device);
+
+  const size_t npix = size_t(H) * W;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  alloc((void**)&s->obs[0], sizeof(float) * npix * Mz);
+  alloc((void**)&s->obs[1], sizeof(float) * npix * Mz);
+  alloc((void**)&s->Astate, sizeof(float) * npix * s->kpad);
+  alloc((void**)&s->frame, sizeof(float) * npix);
+  alloc((void**)&s->whitened, sizeof(float) * npix);
+  alloc((void**)&s->vx, sizeof(float) * npix);
+  alloc((void**)&s->vy, sizeof(float) * npix);
+  alloc((void**)&s->vidx, sizeof(int) * npix);
+  alloc((void**)&s->d_spec, sizeof(SpecTables));
+  if (s->debug) {
+    alloc((void**)&s->d_dump_win, sizeof(float2) * npix * M * M * Mz);
+    alloc((void**)&s->d_dump_pow, sizeof(float) * npix * M * M * Mz);
+  }
+  if (e != cudaSuccess) {
+    int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "cudaMalloc");
+    free_stream(s);
+    return rc;
+  }
+  // tables
+  SpecTables tb;
+  std::vector<int> hg;
+  build_spec_tables(s, tb, hg);
+  std::vector<float2> taby(size_t(L) * M), tabx(size_t(L) * (K + 1));
+  for (int g = 0; g < L; ++g) {
+    const double l = -s->vmax + g * s->vstep;
+    for (int iy = 0; iy < M; ++iy) taby[size_t(g) * M + iy] = cexpf2(2.0 * kPi * (iy - K) * l / M);
+    for (int kx = 0; kx <= K; ++kx) tabx[size_t(g) * (K + 1) + kx] = cexpf2(2.0 * kPi * kx * l / M);
+  }
+  const int Wb = 2 * s->B + 1;
+  const double hscale = std::sqrt(double(Wb) * Wb / (double(M) * M * Mz));
+  std::vector<float> hw(size_t(L) * Mz * M);
+  for (int g = 0; g < L; ++g) {
+    const double v = -s->vmax + g * s->vstep;
+    for (int m = 0; m < Mz; ++m)
+      for (int j = 0; j < M; ++j) {
+        const int d = j - K;
+        hw[(size_t(g) * Mz + m) * M + j] = float(hscale * dirichlet(Wb, (d + v * (m - s->mpz)) / M));
+      }
+  }
+  alloc((void**)&s->d_hgather, sizeof(int) * hg.size());
+  alloc((void**)&s->d_taby, sizeof(float2) * taby.size());
+  alloc((void**)&s->d_tabx, sizeof(float2) * tabx.size());
+  alloc((void**)&s->d_hw, sizeof(float) * hw.size());
+  if (e != cudaSuccess) {
+    int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "cudaMalloc");
+    free_stream(s);
+    return rc;
+  }
+  cudaError_t c1 = cudaMemcpy(s->d_spec, &tb, sizeof(tb), cudaMemcpyHostToDevice);
+  cudaError_t c2 = cudaMemcpy(s->d_hgather, hg.data(), sizeof(int) * hg.size(), cudaMemcpyHostToDevice);
+  cudaError_t c3 = cudaMemcpy(s->d_taby, taby.data(), sizeof(float2) * taby.size(), cudaMemcpyHostToDevice);
+  cudaError_t c4 = cudaMemcpy(s->d_tabx, tabx.data(), sizeof(float2) * tabx.size(), cudaMemcpyHostToDevice);
+  cudaError_t c5 = cudaMemcpy(s->d_hw, hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice);
+  for (cudaError_t c : {c1, c2, c3, c4, c5})
+    if (c != cudaSuccess) {
+      int rc = set_cuda_err(c, "cudaMemcpy(tables)");
+      free_stream(s);
+      return rc;
+    }
+  // the phase-D task split must fit the kernel's per-thread budget
+  const int nthr = spectrum_threads(M, Mz, s->tw);
+  if (s->tw * ((M * M - 1) / 2 + 1) > 4 * nthr || spectrum_smem(M, Mz, s->tw) > 227 * 1024) {
+    free_stream(s);
+    return WH_EUNSUP;
+  }
+  int rc = wh_reset_stream(s);
+  if (rc != WH_OK) {
+    free_stream(s);
+    return rc;
+  }
+  *out = s;
+  return WH_OK;
+}
+
+int wh_reset_stream(wh_stream* s) {
+  if (!s) return WH_EINVAL;
+  const size_t npix = size_t(s->H) * s->W;
+  WH_CU(cudaMemsetAsync(s->obs[0], 0, sizeof(float) * npix * s->Mz, s->st));
+  WH_CU(cudaMemsetAsync(s->obs[1], 0, sizeof(float) * npix * s->Mz, s->st));
+  WH_CU(cudaMemsetAsync(s->Astate, 0, sizeof(float) * npix * s->kpad, s->st));
+  WH_CU(cudaMemsetAsync(s->whitened, 0, sizeof(float) * npix, s->st));
+  WH_CU(cudaMemsetAsync(s->vidx, 0, sizeof(int) * npix, s->st));
+  s->t = 0;
+  s->cur = 0;
+  return WH_OK;
+}
+
+int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
+  if (!s || !frame) return WH_EINVAL;
+  const size_t npix = size_t(s->H) * s->W;
+  const float* src = frame;
+  if (!is_device) {
+    WH_CU(cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, s->st));
+    src = s->frame;
+  }
+  cudaEvent_t* ev = nullptr;
+  if (s->prof && s->ev_used + 4 <= 4 * 65536) {
+    while (s->ev.size() < s->ev_used + 4) {
+      cudaEvent_t e;
+      WH_CU(cudaEventCreate(&e));
+      s->ev.push_back(e);
+    }
+    ev = &s->ev[s->ev_used];
+    s->ev_used += 4;
+  }
+  if (ev) WH_CU(cudaEventRecord(ev[0], s->st));
+  SpecArgs sa;
+  sa.H = s->H; sa.W = s->W; sa.M = s->M; sa.Mz = s->Mz; sa.tw = s->tw; sa.th = s->th;
+  sa.kpad = s->kpad; sa.alpha = float(s->alpha); sa.frame = src;
+  sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
+  sa.tables = s->d_spec; sa.hgather = s->d_hgather;
+  sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
+  cudaError_t e = launch_spectrum(sa, s->st);
+  if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
+  if (ev) WH_CU(cudaEventRecord(ev[1], s->st));
+  AutocorrArgs aa;
+  aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
+  aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
+  aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
+  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
+  e = launch_autocorr(aa, s->st);
+  if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
+  if (ev) WH_CU(cudaEventRecord(ev[2], s->st));
+  PefArgs pa;
+  pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
+  pa.obs = s->obs[1 - s->cur]; pa.vidx = s->vidx; pa.hw = s->d_hw; pa.whitened = s->whitened;
+  e = launch_pef(pa, s->st);
+  if (e != cudaSuccess) return set_cuda_err(e, "PEF kernel");
+  if (ev) WH_CU(cudaEventRecord(ev[3], s->st));
+  g_launches.fetch_add(3);
+  s->cur = 1 - s->cur;
+  s->t += 1;
+  return WH_OK;
+}
+
+static int copy_out(wh_stream* s, void* dst, const void* src, size_t bytes, int is_device) {
+  if (is_device) {
+    WH_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s->st));
+  } else {
+    WH_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
+    WH_CU(cudaStreamSynchronize(s->st));
+  }
+  return WH_OK;
+}
+
+int wh_read_whitened(wh_stream* s, float* out, int is_device, long long* frame_index) {
+  if (!s || !out) return WH_EINVAL;
+  if (s->t < s->mpz + 1) return WH_ENOTREADY;
+  if (frame_index) *frame_index = s->t - 1 - s->mpz;
+  return copy_out(s, out, s->whitened, sizeof(float) * size_t(s->H) * s->W, is_device);
+}
+
+int wh_read_velocity(wh_stream* s, float* vx, float* vy, int* vidx, int is_device,
+                     long long* frame_index) {
+  if (!s) return WH_EINVAL;
+  if (s->t < 1) return WH_ENOTREADY;
+  if (frame_index) *frame_index = s->t - 1;
+  const size_t n = size_t(s->H) * s->W;
+  int rc = WH_OK;
+  if (vx && (rc = copy_out(s, vx, s->vx, sizeof(float) * n, is_device)) != WH_OK) return rc;
+  if (vy && (rc = copy_out(s, vy, s->vy, sizeof(float) * n, is_device)) != WH_OK) return rc;
+  if (vidx && (rc = copy_out(s, vidx, s->vidx, sizeof(int) * n, is_device)) != WH_OK) return rc;
+  return WH_OK;
+}
+
+int wh_read_spectrum(wh_stream* s, int kind, void* out, int is_device) {
+  if (!s || !out) return WH_EINVAL;
+  if (s->t < 1) return WH_ENOTREADY;
+  const size_t nb = size_t(s->H) * s->W * s->M * s->M * s->Mz;
+  if (kind == WH_SPEC_RAW) {
+    if (!s->d_raw) WH_CU(cudaMalloc((void**)&s->d_raw, sizeof(float2) * nb));
+    RawSpecArgs ra;
+    ra.H = s->H; ra.W = s->W; ra.M = s->M; ra.Mz = s->Mz; ra.obs = s->obs[s->cur]; ra.out = s->d_raw;
+    cudaError_t e = launch_raw_spectrum(ra, s->st);
+    if (e != cudaSuccess) return set_cuda_err(e, "raw spectrum kernel");
+    g_launches.fetch_add(1);
+    return copy_out(s, out, s->d_raw, sizeof(float2) * nb, is_device);
+  }
+  if (!s->debug) return WH_EINVAL;
+  if (kind == WH_SPEC_WINDOWED) return copy_out(s, out, s->d_dump_win, sizeof(float2) * nb, is_device);
+  if (kind == WH_SPEC_POWER) return copy_out(s, out, s->d_dump_pow, sizeof(float) * nb, is_device);
+  return WH_EINVAL;
+}
+
+int wh_read_autocorr(wh_stream* s, float* out, int is_device) {
+  if (!s || !out) return WH_EINVAL;
+  if (s->t < 1) return WH_ENOTREADY;
+  const size_t n = size_t(s->H) * s->W * s->L * s->L;
+  if (!s->d_rs) WH_CU(cudaMalloc((void**)&s->d_rs, sizeof(float) * n));
+  AutocorrArgs aa;
+  aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
+  aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
+  aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = s->d_rs;
+  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
+  cudaError_t e = launch_autocorr(aa, s->st);
+  if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
+  g_launches.fetch_add(1);
+  return copy_out(s, out, s->d_rs, sizeof(float) * n, is_device);
+}
+
+int wh_stream_info(const wh_stream* s, int* grid_len, int* delay_z, int* band,
+                   long long* frames_pushed) {
+  if (!s) return WH_EINVAL;
+  if (grid_len) *grid_len = s->L;
+  if (delay_z) *delay_z = s->mpz;
+  if (band) *band = s->B;
+  if (frames_pushed) *frames_pushed = s->t;
+  return WH_OK;
+}
+
+int wh_output_pointers(wh_stream* s, float** whitened, float** vx, float** vy, int** vidx) {
+  if (!s) return WH_EINVAL;
+  if (whitened) *whitened = s->whitened;
+  if (vx) *vx = s->vx;
+  if (vy) *vy = s->vy;
+  if (vidx) *vidx = s->vidx;
+  return WH_OK;
+}
+
+int wh_profile_enable(wh_stream* s, int on) {
+  if (!s) return WH_EINVAL;
+  s->prof = on ? 1 : 0;
+  return WH_OK;
+}
+
+int wh_profile_read(wh_stream* s, double* ms, long long* n, int reset) {
+  if (!s) return WH_EINVAL;
+  WH_CU(cudaStreamSynchronize(s->st));
+  double acc[3] = {0, 0, 0};
+  for (size_t f = 0; f + 4 <= s->ev_used; f += 4)
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      WH_CU(cudaEventElapsedTime(&t, s->ev[f + k], s->ev[f + k + 1]));
+      acc[k] += t;
+    }
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (n) n[k] = (long long)(s->ev_used / 4);
+  }
+  if (reset) s->ev_used = 0;
+  return WH_OK;
+}
+
+int wh_destroy_stream(wh_stream* s) {
+  if (!s) return WH_OK;
+  cudaStreamSynchronize(s->st);
+  free_stream(s);
+  return WH_OK;
+}
+
+const char* wh_status_string(int st) {
+  switch (st) {
+    case WH_OK: return "ok";
+    case WH_EINVAL: return "invalid argument";
+    case WH_ENOMEM: return "out of memory";
+    case WH_EADMIT: return "over the memory budget (not admitted)";
+    case WH_ENOTREADY: return "output not ready (too few frames pushed)";
+    case WH_ECUDA: return "CUDA error";
+    case WH_ETIMEOUT: return "device wait timed out";
+    case WH_EUNSUP: return "unsupported parameter combination";
+    default: return "unknown status";
+  }
+}
+
+const char* wh_last_error(void) { return g_err; }
+
+long long wh_kernel_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

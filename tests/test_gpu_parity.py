@@ -1,0 +1,96 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs (needs a B300).
+
+Cases span several tiles and a ragged tail, frames smaller than the window,
+odd and even temporal orders, and the full 512 x 640 configuration in the
+launch configuration the benchmark times (sampled pixels).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1408_3526_b300 import scenes
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=True, **kw):
+    T, H, W = frames.shape
+    g = P.run_gpu(frames, M, Mz, vmax, step, spec_frames=spec_frames, debug=debug, **kw)
+    o = oracle.Oracle(M, Mz, vmax, step, B=kw.get("band"), mpz=kw.get("delay_z"),
+                      alpha=kw.get("alpha"))
+    ref = o.run(frames, spec_frames=list(spec_frames), spectrum=True, power=debug,
+                autocorr=True, windowed=debug)
+    for i, t in enumerate(spec_frames):
+        assert P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][i]) <= P.SPEC_TOL
+        if debug:
+            assert P.spectrum_rel_err(g["windowed"][t], ref["windowed"][i]) <= P.SPEC_TOL
+            assert P.spectrum_rel_err(g["power"][t], ref["power"][i]) <= 2 * P.SPEC_TOL
+        ar = ref["autocorr"][i]
+        scale = np.abs(ar).reshape(H, W, -1).max(-1)[..., None, None]
+        assert np.max(np.abs(g["autocorr"][t] - ar) / np.maximum(scale, 1e-30)) <= P.SPEC_TOL
+    rs = {t: ref["autocorr"][i] for i, t in enumerate(spec_frames)}
+    frac, steps, tie = P.velocity_report(g["vel_index"], ref["vel_index"], rs, o.L)
+    if check_vel_frac:
+        assert frac >= P.VEL_EXACT_FRAC, frac
+    assert steps <= 1
+    assert tie <= P.TIE_TOL, tie
+    # whitened output for the GPU's velocity field
+    ref2 = o.run(frames, vel_override=g["vel_index"], velocity=False)
+    err = P.whitened_err(g["whitened"], ref2["whitened"], frames, o.mpz)
+    assert err <= P.WHITE_TOL_REL, err
+    return g, ref
+
+
+def test_parity_config1_full():
+    """64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2 step 1/4 (in full)."""
+    sc = scenes.config1_scene(T=32)
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31))
+
+
+def test_parity_config2_shape_crop():
+    """15 x 15 window, order 6, grid +-3 step 1/4 on a 40 x 56 crop of the
+    non-uniform-flow scene (several tiles, ragged tail)."""
+    sc = scenes.config2_scene(T=14, H=512, W=640)
+    fr = np.ascontiguousarray(sc.frames[:, 200:240, 300:356])
+    _compare(fr, 15, 6, 3.0, 0.25, spec_frames=(13,))
+
+
+@pytest.mark.parametrize("M,Mz,H,W", [(7, 5, 37, 53), (5, 3, 33, 70), (9, 6, 19, 41)])
+def test_parity_ragged_odd_even_orders(M, Mz, H, W):
+    sc = scenes.small_scene(T=12, H=H, W=W, seed=M * 10 + Mz, vx=0.6, vy=-0.3, tex_size=128)
+    _compare(sc.frames, M, Mz, 1.5, 0.5, spec_frames=(Mz - 1, 11))
+
+
+def test_parity_frame_smaller_than_window():
+    sc = scenes.small_scene(T=8, H=5, W=7, seed=3, tex_size=64)
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(7,), check_vel_frac=False)
+
+
+def test_parity_full_size_config2_sampled():
+    """512 x 640, 15 x 15, order 6, grid +-3/0.25: full frames on the GPU, the
+    oracle on sampled pixels (edges, corners, interior) over every frame."""
+    T = 20
+    sc = scenes.config2_scene(T=T)
+    H, W = 512, 640
+    g = P.run_gpu(sc.frames, 15, 6, 3.0, 0.25, spec_frames=(T - 1,), debug=False)
+    o = oracle.Oracle(15, 6, 3.0, 0.25)
+    rng = np.random.default_rng(0)
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (7, 300), (255, 319), (511, 17)]
+    pts += [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(9)]
+    same = 0
+    for (y, x) in pts:
+        ref = o.run(sc.frames, crop=(y, x, 1, 1), spec_frames=[T - 1], spectrum=True, autocorr=True)
+        assert P.spectrum_rel_err(g["spectrum"][T - 1][y:y + 1, x:x + 1],
+                                  ref["spectrum"][0]) <= P.SPEC_TOL
+        ar = ref["autocorr"][0]
+        assert np.max(np.abs(g["autocorr"][T - 1][y, x] - ar[0, 0])) <= P.SPEC_TOL * np.abs(ar).max()
+        gi = g["vel_index"][:, y:y + 1, x:x + 1]
+        same += int(np.sum(gi == ref["vel_index"]))
+        d = np.abs(gi % o.L - ref["vel_index"] % o.L) + 0
+        assert np.all(np.maximum(d, np.abs(gi // o.L - ref["vel_index"] // o.L)) <= 1)
+        ref2 = o.run(sc.frames, crop=(y, x, 1, 1), vel_override=np.ascontiguousarray(gi),
+                     velocity=False)
+        err = P.whitened_err(g["whitened"][:, y:y + 1, x:x + 1], ref2["whitened"], sc.frames, o.mpz)
+        assert err <= P.WHITE_TOL_REL
+    assert same >= 0.99 * T * len(pts)
