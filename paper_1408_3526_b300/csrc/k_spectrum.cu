@@ -52,7 +52,7 @@ __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n
 // Byte offsets of the shared-memory arrays (16-byte aligned each); the same
 // function sizes the launch on the host.
 struct SpecSmem {
-  size_t twr, ring, xc, pbuf, hg, wres, cph, total;
+  size_t twr, ring, xc, pbuf, hg, wres, cph, off, total;
 };
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
@@ -74,8 +74,56 @@ __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
   L.hg = o;   o = align16(o + sizeof(int) * size_t(nh + 1) * nslot);
   L.wres = o; o = align16(o + sizeof(float2) * M);
   L.cph = o;  o = align16(o + sizeof(float2) * M);
+  L.off = o;  o = align16(o + sizeof(float2) * npl);
   L.total = o;
   return L;
+}
+
+// Observer update of one pixel (frame value pa[0], packed T_{t-1} in pa[1..Mz])
+// -> T_t (packed, written back into T) and its Hann-windowed planes Tw.
+template <int M, int MZ>
+__device__ __forceinline__ void observer_hann(const float* pa, const float2* lam, float2 hz,
+                                              float2 (&T)[Geo<M, MZ>::NPL],
+                                              float2 (&Tw)[Geo<M, MZ>::NPL]) {
+  using G = Geo<M, MZ>;
+  constexpr int J = G::J, NPL = G::NPL;
+  constexpr bool EVEN = G::EVEN;
+  const float xin = pa[0];
+  T[0] = make_float2(pa[1], 0.f);
+#pragma unroll
+  for (int j = 1; j <= J; ++j) T[j] = make_float2(pa[2 * j], pa[2 * j + 1]);
+  if (EVEN) T[NPL - 1] = make_float2(pa[MZ], 0.f);
+  // prior s = lambda T_{t-1}; prediction = sum over all Mz bins (Hermitian)
+  float2 s[NPL];
+  float yhat = 0.f;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    s[p] = cmul(lam[p], T[p]);
+    const bool real = (p == 0) || (EVEN && p == NPL - 1);
+    yhat += real ? s[p].x : 2.f * s[p].x;
+  }
+  const float e = (xin - yhat) * (1.0f / MZ);
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    T[p] = make_float2(s[p].x + e, s[p].y);
+    const bool real = (p == 0) || (EVEN && p == NPL - 1);
+    if (real) T[p].y = 0.f;
+  }
+  // Hann along kz: Tw(p) = 1/2 T(p) + 1/4 hz T(p+1) + 1/4 conj(hz) T(p-1), bins mod Mz
+  float2 Tf[MZ];
+  Tf[0] = T[0];
+#pragma unroll
+  for (int j = 1; j <= J; ++j) { Tf[j] = T[j]; Tf[MZ - j] = conjf2(T[j]); }
+  if (EVEN) Tf[MZ / 2] = T[NPL - 1];
+#pragma unroll
+  for (int p = 0; p < NPL; ++p) {
+    const float2 up = Tf[(p + 1) % MZ], dn = Tf[(p + MZ - 1) % MZ];
+    float2 tw = cadd(cscale(Tf[p], 0.5f),
+                     cadd(cscale(cmul(hz, up), 0.25f), cscale(cmul(conjf2(hz), dn), 0.25f)));
+    const bool real = (p == 0) || (EVEN && p == NPL - 1);
+    if (real) tw.y = 0.f;
+    Tw[p] = tw;
+  }
 }
 
 template <int M, int MZ>
@@ -100,6 +148,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
   int* hg = reinterpret_cast<int*>(smem_raw + SL.hg);                 // [(nh+1)][nslot]
   float2* wres = reinterpret_cast<float2*>(smem_raw + SL.wres);       // [M]
   float2* cph = reinterpret_cast<float2*>(smem_raw + SL.cph);         // [M]
+  float2* offs = reinterpret_cast<float2*>(smem_raw + SL.off);        // [NPL]
 
   for (int i = tid; i < nch * M; i += nthr) xc[i] = tb.xcoef[i / M][i % M];
   for (int i = tid; i < (nh + 1) * nslot; i += nthr) hg[i] = a.hgather[i];
@@ -109,7 +158,6 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
   for (int p = 0; p < NPL; ++p) lam[p] = tb.lam[p];
 
   const float2 hz = tb.hann_z;
-  const float invMz = 1.0f / MZ;
   const float alpha = a.alpha, oma = 1.0f - alpha;
   const float sP = float(MZ) * float(MZ) / float(M * M * MZ);   // (Mz/sqrt(N))^2
 
@@ -136,6 +184,18 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
     }
   };
   loadA(0);
+  // Per-plane offset removed from every Tw of this CTA before the spatial sums.
+  // The high-passed, Hann-windowed spectrum is exactly invariant to a spatially
+  // constant offset per temporal plane (it only feeds the removed kx = ky = 0
+  // bin and the correction that cancels its window leakage), so subtracting
+  // one constant per CTA leaves the result unchanged while keeping the FP32
+  // sums at the scale of the texture instead of the scene's DC level.
+  if (tid == 0) {
+    float2 Tn[NPL], Tw0[NPL];
+    observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
+  }
 
   // ---- phase-D prefetch (first output row y0) ----------------------------------
   const int ntD = TW * (nh + 1);
@@ -163,28 +223,8 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
     const int r = y0 - K + i;               // input row (unclamped)
     // ---------------- A: observer update + Hann along kz ---------------------
     if (tid < RW) {
-      const float xin = pa[0];
-      float2 T[NPL];
-      T[0] = make_float2(pa[1], 0.f);
-#pragma unroll
-      for (int j = 1; j <= J; ++j) T[j] = make_float2(pa[2 * j - 1 + 1], pa[2 * j + 1]);
-      if (EVEN) T[NPL - 1] = make_float2(pa[MZ], 0.f);
-      // prior s = lambda T_{t-1}; prediction = sum over all Mz bins (Hermitian)
-      float2 s[NPL];
-      float yhat = 0.f;
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) {
-        s[p] = cmul(lam[p], T[p]);
-        const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        yhat += real ? s[p].x : 2.f * s[p].x;
-      }
-      const float e = (xin - yhat) * invMz;
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) {
-        T[p] = make_float2(s[p].x + e, s[p].y);
-        const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        if (real) T[p].y = 0.f;
-      }
+      float2 T[NPL], Tw[NPL];
+      observer_hann<M, MZ>(pa, lam, hz, T, Tw);
       // owner writes the new state
       const int xs = x0 - K + tid;
       if (r >= y0 && r < y0 + TH && r < H && tid >= K && tid < K + TW && xs < W) {
@@ -197,21 +237,8 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
         }
         if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
       }
-      // Hann along kz: Tw(p) = 1/2 T(p) + 1/4 hz T(p+1) + 1/4 conj(hz) T(p-1), mod Mz
-      float2 Tf[MZ];
-      Tf[0] = T[0];
 #pragma unroll
-      for (int j = 1; j <= J; ++j) { Tf[j] = T[j]; Tf[MZ - j] = conjf2(T[j]); }
-      if (EVEN) Tf[MZ / 2] = T[NPL - 1];
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) {
-        const float2 up = Tf[(p + 1) % MZ], dn = Tf[(p + MZ - 1) % MZ];
-        float2 tw = cadd(cscale(Tf[p], 0.5f),
-                         cadd(cscale(cmul(hz, up), 0.25f), cscale(cmul(conjf2(hz), dn), 0.25f)));
-        const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        if (real) tw.y = 0.f;
-        twr[p * RW + tid] = tw;
-      }
+      for (int p = 0; p < NPL; ++p) twr[p * RW + tid] = csub(Tw[p], offs[p]);
     }
     if (i + 1 < nrows) loadA(i + 1);
     __syncthreads();

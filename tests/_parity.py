@@ -60,9 +60,15 @@ def spectrum_rel_err(gpu, ref):
     return float(np.max(err / np.maximum(rms, 1e-30)))
 
 
-def velocity_report(gpu_idx, ref_idx, ref_rs_frames, L):
+def velocity_report(gpu_idx, ref_idx, ref_rs_frames, L, first=1):
     """Fraction identical, max grid-step distance, and whether the mismatches
-    at frames with stored R' are near ties of the oracle's R'."""
+    at frames with stored R' are near ties of the oracle's R'.
+
+    Frame 0 is excluded: with one frame of (zero-padded) history the lz = 1
+    slice of R is exactly zero for every l, a complete tie that each side
+    breaks by its own rounding noise."""
+    gpu_idx, ref_idx = gpu_idx[first:], ref_idx[first:]
+    ref_rs_frames = {t - first: v for t, v in ref_rs_frames.items() if t >= first}
     same = gpu_idx == ref_idx
     gx, gy = gpu_idx % L, gpu_idx // L
     rx, ry = ref_idx % L, ref_idx // L
@@ -75,7 +81,8 @@ def velocity_report(gpu_idx, ref_idx, ref_rs_frames, L):
         at_gpu = np.take_along_axis(flat, gpu_idx[t][..., None].astype(np.int64), -1)[..., 0]
         gap = (mx - at_gpu) / np.maximum(scale, 1e-300)
         worst_tie = max(worst_tie, float(gap.max()))
-    return float(same.mean()), int(steps.max()), worst_tie
+    bad = [(int(t), int(np.sum(~same[t]))) for t in range(same.shape[0]) if not same[t].all()]
+    return float(same.mean()), int(steps.max()), worst_tie, bad
 
 
 def whitened_err(gpu_w, ref_w, frames, delay):

@@ -21,23 +21,30 @@ def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=
                       alpha=kw.get("alpha"))
     ref = o.run(frames, spec_frames=list(spec_frames), spectrum=True, power=debug,
                 autocorr=True, windowed=debug)
+    m = {"spec": 0.0, "win": 0.0, "pow": 0.0, "rs": 0.0}
     for i, t in enumerate(spec_frames):
-        assert P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][i]) <= P.SPEC_TOL
+        m["spec"] = max(m["spec"], P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][i]))
         if debug:
-            assert P.spectrum_rel_err(g["windowed"][t], ref["windowed"][i]) <= P.SPEC_TOL
-            assert P.spectrum_rel_err(g["power"][t], ref["power"][i]) <= 2 * P.SPEC_TOL
+            m["win"] = max(m["win"], P.spectrum_rel_err(g["windowed"][t], ref["windowed"][i]))
+            m["pow"] = max(m["pow"], P.spectrum_rel_err(g["power"][t], ref["power"][i]))
         ar = ref["autocorr"][i]
         scale = np.abs(ar).reshape(H, W, -1).max(-1)[..., None, None]
-        assert np.max(np.abs(g["autocorr"][t] - ar) / np.maximum(scale, 1e-30)) <= P.SPEC_TOL
+        m["rs"] = max(m["rs"], float(np.max(np.abs(g["autocorr"][t] - ar) / np.maximum(scale, 1e-30))))
     rs = {t: ref["autocorr"][i] for i, t in enumerate(spec_frames)}
-    frac, steps, tie = P.velocity_report(g["vel_index"], ref["vel_index"], rs, o.L)
-    if check_vel_frac:
-        assert frac >= P.VEL_EXACT_FRAC, frac
-    assert steps <= 1
-    assert tie <= P.TIE_TOL, tie
-    # whitened output for the GPU's velocity field
+    frac, steps, tie, bad = P.velocity_report(g["vel_index"], ref["vel_index"], rs, o.L)
     ref2 = o.run(frames, vel_override=g["vel_index"], velocity=False)
     err = P.whitened_err(g["whitened"], ref2["whitened"], frames, o.mpz)
+    print(f"\n[parity M={M} Mz={Mz} {T}x{H}x{W}] spec {m['spec']:.2e} windowed {m['win']:.2e} "
+          f"power {m['pow']:.2e} R' {m['rs']:.2e} vel_same {frac:.5f} max_steps {steps} "
+          f"tie {tie:.2e} whitened {err:.2e} xRMS mismatches {bad[:6]}", flush=True)
+    assert m["spec"] <= P.SPEC_TOL
+    assert m["win"] <= P.SPEC_TOL
+    assert m["pow"] <= 2 * P.SPEC_TOL
+    assert m["rs"] <= P.SPEC_TOL
+    if check_vel_frac:
+        assert frac >= P.VEL_EXACT_FRAC, (frac, bad)
+    assert steps <= 1, (steps, bad)
+    assert tie <= P.TIE_TOL, (tie, bad)
     assert err <= P.WHITE_TOL_REL, err
     return g, ref
 
@@ -86,11 +93,12 @@ def test_parity_full_size_config2_sampled():
         ar = ref["autocorr"][0]
         assert np.max(np.abs(g["autocorr"][T - 1][y, x] - ar[0, 0])) <= P.SPEC_TOL * np.abs(ar).max()
         gi = g["vel_index"][:, y:y + 1, x:x + 1]
-        same += int(np.sum(gi == ref["vel_index"]))
-        d = np.abs(gi % o.L - ref["vel_index"] % o.L) + 0
-        assert np.all(np.maximum(d, np.abs(gi // o.L - ref["vel_index"] // o.L)) <= 1)
+        ri = ref["vel_index"]
+        same += int(np.sum(gi[1:] == ri[1:]))          # frame 0: exact tie, see _parity
+        d = np.maximum(np.abs(gi % o.L - ri % o.L), np.abs(gi // o.L - ri // o.L))
+        assert np.all(d[1:] <= 1), (y, x, d.ravel())
         ref2 = o.run(sc.frames, crop=(y, x, 1, 1), vel_override=np.ascontiguousarray(gi),
                      velocity=False)
         err = P.whitened_err(g["whitened"][:, y:y + 1, x:x + 1], ref2["whitened"], sc.frames, o.mpz)
         assert err <= P.WHITE_TOL_REL
-    assert same >= 0.99 * T * len(pts)
+    assert same >= 0.99 * (T - 1) * len(pts)
