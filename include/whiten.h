@@ -60,7 +60,7 @@ extern "C" {
 
 /* Velocity grid: {-vmax, -vmax + step, ..., +vmax} on both axes
  * (Sec. 3: l_x = l_y = [-8 .. 8]/4, a 17 x 17 grid at vmax = 2, step 1/4).
- * vmax must be an integer multiple of step; L = 2 vmax/step + 1 <= 33. */
+ * vmax must be an integer multiple of step; L = 2 vmax/step + 1 <= 31. */
 typedef struct {
     float vmax;
     float step;

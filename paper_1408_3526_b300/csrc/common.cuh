@@ -18,7 +18,7 @@ namespace wh {
 
 constexpr int kMaxM = 15;
 constexpr int kMaxMz = 8;
-constexpr int kMaxL = 33;
+constexpr int kMaxL = 31;
 constexpr int kMaxPlanes = kMaxMz / 2 + 1;
 constexpr int kMaxChan = 2 * (kMaxM) + (kMaxPlanes) * kMaxM + kMaxPlanes;
 

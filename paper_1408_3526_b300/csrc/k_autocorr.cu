@@ -1,92 +1,150 @@
-// Autocorrelation on the velocity grid + argmax, FP32 on CUDA cores.
+// Autocorrelation on the velocity grid + argmax, exact FP32 on CUDA cores.
 //
 // Eq. (10) on the lz = 1 slice: R(l) = sum_k P(k) cos(2pi(kx lx/M + ky ly/M + kz/Mz)).
 // With A_c/A_s the kz-reduced (and smoothed) power held in the stream state,
 // Q(kx,ky) = A_c + j A_s satisfies Q(-k) = conj(Q(k)) and
-//   R(lx,ly) = Re sum_{kx,ky} Q(kx,ky) e^{j2pi(kx lx + ky ly)/M}
-//            = Re T(0,ly) + 2 sum_{kx=1..K} Re(e^{j2pi kx lx/M} T(kx,ly)),
-//   T(kx,ly) = sum_{ky=-K..K} Q(kx,ky) e^{j2pi ky ly/M},
-// evaluated separably (two small complex contractions per pixel).  The
-// velocity is the grid point of the largest R (Sec. 2: v = l/lz, lz = 1);
-// ties go to the lowest flat index iy*L + ix.
+//   R(lx,ly) = Re T(0,ly) + 2 sum_{kx=1..K} Re(e^{j2pi kx lx/M} T(kx,ly)),
+//   T(kx,ly) = sum_{ky=-K..K} Q(kx,ky) e^{j2pi ky ly/M}.
+// The grid is symmetric (l and -l both on it), so with
+//   a = Qr(kx,0) + sum_{ky>0} (Qr(ky)+Qr(-ky)) cos,  b = sum_{ky>0} (Qi(ky)-Qi(-ky)) sin,
+//   c = sum_{ky>0} (Qr(ky)-Qr(-ky)) sin,             d = Qi(kx,0) + sum_{ky>0} (Qi(ky)+Qi(-ky)) cos
+// one pass gives T(kx,+ly) = (a-b, c+d) and T(kx,-ly) = (a+b, d-c); likewise
+// one pass over kx gives R(+lx,ly) and R(-lx,ly).  The velocity is the grid
+// point of the largest R (v = l/lz, lz = 1); ties go to the lowest flat
+// index iy*L + ix.
 //
-// One warp per pixel; Q and T live in shared memory.
+// Mapping: a warp works on two pixels, one per half-warp.  Stage 1: lane j
+// owns ly = +-l_j (twiddles for its ly in registers) and reads the pixel's
+// Q sums from shared memory by broadcast.  Stage 2: lane j owns lx = +-l_j
+// and reads T(., ly) by broadcast.
 #include "common.cuh"
 
 namespace wh {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kHalf = 16;   // lanes per pixel; the grid half-length (L+1)/2 must fit
 
+template <int M>
+struct AcSmem {
+  static constexpr int K = (M - 1) / 2;
+  // per pixel: Q sums [K+1][K] x 4 (sr, dr, si, di) + Q(kx,0) [K+1] x 2
+  static constexpr int kQ = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;   // 16-byte multiple
+};
+
+template <int M>
 __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArgs a) {
-  const int M = a.M, K = (a.M - 1) / 2, L = a.L, nh = (a.M * a.M - 1) / 2;
+  constexpr int K = (M - 1) / 2;
+  constexpr int QN = AcSmem<M>::kQ;
+  const int L = a.L, Lh = (L + 1) / 2, gc = (L - 1) / 2, nh = (M * M - 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int half = lane >> 4, j = lane & 15;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* ty = reinterpret_cast<float2*>(smem_raw);     // [L][M]
-  float2* tx = ty + L * M;                               // [L][K+1]
-  float2* Qall = tx + L * (K + 1);                       // [warps][K+1][M]
-  float2* Tall = Qall + kWarps * (K + 1) * M;            // [warps][K+1][L]
-  for (int i = threadIdx.x; i < L * M; i += blockDim.x) ty[i] = a.tab_y[i];
-  for (int i = threadIdx.x; i < L * (K + 1); i += blockDim.x) tx[i] = a.tab_x[i];
-  __syncthreads();
-
+  float* qbuf = reinterpret_cast<float*>(smem_raw) + (wid * 2 + half) * QN;            // [QN]
+  float2* tbuf = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem_raw) + kWarps * 2 * QN) +
+                 (wid * 2 + half) * (K + 1) * L;                                        // [K+1][L]
+  // lane-owned twiddles: cos/sin(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
+  float cw[K], sw[K];
+  const bool act = j < Lh;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 e = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
+    cw[k] = e.x;
+    sw[k] = e.y;
+  }
   const long long npix = (long long)a.H * a.W;
-  float2* Q = Qall + wid * (K + 1) * M;
-  float2* T = Tall + wid * (K + 1) * L;
-  for (long long pix = (long long)blockIdx.x * kWarps + wid; pix < npix;
-       pix += (long long)gridDim.x * kWarps) {
-    const float* A = a.Astate + pix * a.kpad;
-    // Q(kx, ky) for kx = 0..K, ky = -K..K
-    for (int e = lane; e < (K + 1) * M; e += 32) {
-      const int kx = e / M, iy = e % M, ky = iy - K;
-      float2 q;
-      if (kx == 0) {
-        if (ky == 0) q = make_float2(A[0], 0.f);
-        else {
-          const int hi = ky > 0 ? ky : -ky;
-          q = make_float2(A[hi], ky > 0 ? A[nh + hi] : -A[nh + hi]);
+  for (long long base = ((long long)blockIdx.x * kWarps + wid) * 2; base < npix;
+       base += (long long)gridDim.x * kWarps * 2) {
+    const long long pix = base + half;
+    const bool valid = pix < npix;
+    // ---- Q sums of this half-warp's pixel ----------------------------------
+    if (valid) {
+      const float* A = a.Astate + pix * a.kpad;
+      for (int e = j; e < (K + 1) * K; e += kHalf) {
+        const int kx = e / K, ky = e % K + 1;
+        float sr, dr, si, di;
+        if (kx == 0) {
+          sr = 2.f * A[ky];
+          dr = 0.f;
+          si = 0.f;
+          di = 2.f * A[nh + ky];
+        } else {
+          const int hp = K + (kx - 1) * M + (ky + K) + 1, hm = K + (kx - 1) * M + (-ky + K) + 1;
+          const float rp = A[hp], rm = A[hm], ip = A[nh + hp], im = A[nh + hm];
+          sr = rp + rm; dr = rp - rm; si = ip + im; di = ip - im;
         }
-      } else {
-        const int hi = K + (kx - 1) * M + iy + 1;
-        q = make_float2(A[hi], A[nh + hi]);
+        qbuf[4 * e + 0] = sr;
+        qbuf[4 * e + 1] = dr;
+        qbuf[4 * e + 2] = si;
+        qbuf[4 * e + 3] = di;
       }
-      Q[e] = q;
+      if (j <= K) {
+        const int kx = j;
+        float qr, qi;
+        if (kx == 0) { qr = A[0]; qi = 0.f; }
+        else {
+          const int h0 = K + (kx - 1) * M + K + 1;
+          qr = A[h0];
+          qi = A[nh + h0];
+        }
+        qbuf[4 * (K + 1) * K + 2 * kx] = qr;
+        qbuf[4 * (K + 1) * K + 2 * kx + 1] = qi;
+      }
     }
     __syncwarp();
-    for (int e = lane; e < (K + 1) * L; e += 32) {
-      const int kx = e / L, gl = e % L;
-      const float2* qr = Q + kx * M;
-      const float2* tr = ty + gl * M;
-      float re = 0.f, im = 0.f;
-      for (int iy = 0; iy < M; ++iy) {
-        const float2 q = qr[iy], w = tr[iy];
-        re = fmaf(q.x, w.x, fmaf(-q.y, w.y, re));
-        im = fmaf(q.x, w.y, fmaf(q.y, w.x, im));
+    // ---- stage 1: T(kx, +-ly_j) ---------------------------------------------
+    if (valid && act) {
+      const float4* q4 = reinterpret_cast<const float4*>(qbuf);
+      const float2* q0 = reinterpret_cast<const float2*>(qbuf + 4 * (K + 1) * K);
+#pragma unroll 2
+      for (int kx = 0; kx <= K; ++kx) {
+        const float2 z = q0[kx];
+        float va = z.x, vb = 0.f, vc = 0.f, vd = z.y;
+#pragma unroll
+        for (int ky = 0; ky < K; ++ky) {
+          const float4 q = q4[kx * K + ky];
+          va = fmaf(q.x, cw[ky], va);
+          vb = fmaf(q.w, sw[ky], vb);
+          vc = fmaf(q.y, sw[ky], vc);
+          vd = fmaf(q.z, cw[ky], vd);
+        }
+        tbuf[kx * L + gc + j] = make_float2(va - vb, vc + vd);
+        tbuf[kx * L + gc - j] = make_float2(va + vb, vd - vc);
       }
-      T[kx * L + gl] = make_float2(re, im);
     }
     __syncwarp();
+    // ---- stage 2: R(+-lx_j, ly) and argmax ------------------------------------
     float best = -INFINITY;
     int bidx = 0x7fffffff;
-    for (int g = lane; g < L * L; g += 32) {
-      const int gy = g / L, gx = g % L;
-      float acc = 0.f;
-      const float2* txr = tx + gx * (K + 1);
-      for (int kx = 1; kx <= K; ++kx) {
-        const float2 t = T[kx * L + gy], w = txr[kx];
-        acc = fmaf(w.x, t.x, fmaf(-w.y, t.y, acc));
+    if (valid && act) {
+      const int gxp = gc + j, gxm = gc - j;
+      for (int gy = 0; gy < L; ++gy) {
+        float v1 = 0.f, v2 = 0.f;
+#pragma unroll
+        for (int kx = 1; kx <= K; ++kx) {
+          const float2 t = tbuf[kx * L + gy];
+          v1 = fmaf(cw[kx - 1], t.x, v1);
+          v2 = fmaf(sw[kx - 1], t.y, v2);
+        }
+        const float t0 = tbuf[gy].x;
+        const float rp = fmaf(2.f, v1 - v2, t0), rm = fmaf(2.f, v1 + v2, t0);
+        const int ip = gy * L + gxp, im = gy * L + gxm;
+        if (a.rs_out) {
+          a.rs_out[pix * (L * L) + ip] = rp;
+          if (j) a.rs_out[pix * (L * L) + im] = rm;
+        }
+        // candidates in increasing flat index within this lane: im < ip
+        if (j && (rm > best || (rm == best && im < bidx))) { best = rm; bidx = im; }
+        if (rp > best || (rp == best && ip < bidx)) { best = rp; bidx = ip; }
       }
-      const float R = fmaf(2.f, acc, T[gy].x);
-      if (a.rs_out) a.rs_out[pix * (L * L) + g] = R;
-      if (R > best) { best = R; bidx = g; }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 8; off > 0; off >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, off);
       const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
     }
-    if (lane == 0) {
+    if (valid && j == 0) {
       a.vidx[pix] = bidx;
       a.vx[pix] = -a.vmax + (bidx % L) * a.vstep;
       a.vy[pix] = -a.vmax + (bidx / L) * a.vstep;
@@ -95,20 +153,34 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   }
 }
 
+template <int M>
+cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
+  constexpr int K = (M - 1) / 2;
+  const size_t smem = sizeof(float) * size_t(kWarps) * 2 * AcSmem<M>::kQ +
+                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * a.L;
+  const long long npix = (long long)a.H * a.W;
+  long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
+  if (blocks > 148LL * 8) blocks = 148LL * 8;
+  cudaError_t e = cudaFuncSetAttribute(autocorr_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem));
+  if (e != cudaSuccess) return e;
+  autocorr_kernel<M><<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st) {
-  const int K = (a.M - 1) / 2;
-  const size_t smem = sizeof(float2) * (size_t(a.L) * a.M + size_t(a.L) * (K + 1) +
-                                        size_t(kWarps) * (K + 1) * (a.M + a.L));
-  long long npix = (long long)a.H * a.W;
-  long long blocks = (npix + kWarps - 1) / kWarps;
-  if (blocks > 148LL * 16) blocks = 148LL * 16;
-  cudaError_t e = cudaFuncSetAttribute(autocorr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem));
-  if (e != cudaSuccess) return e;
-  autocorr_kernel<<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
-  return cudaGetLastError();
+  if ((a.L + 1) / 2 > kHalf || (a.L % 2) == 0) return cudaErrorInvalidValue;
+  switch (a.M) {
+    case 5: return launch_m<5>(a, st);
+    case 7: return launch_m<7>(a, st);
+    case 9: return launch_m<9>(a, st);
+    case 11: return launch_m<11>(a, st);
+    case 13: return launch_m<13>(a, st);
+    case 15: return launch_m<15>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace wh

@@ -37,7 +37,8 @@ namespace {
 
 constexpr int kPrefA = kMaxMz + 1;   // frame + Mz state floats per phase-A pixel
 constexpr int kMaxDTasks = 4;        // phase-D tasks per thread (checked on the host)
-constexpr int kSpecMaxThreads = 768;
+constexpr int kSpecMaxThreads = 384;
+constexpr int kMaxBTasks = 2;        // phase-B tasks per thread (checked on the host)
 
 template <int M, int MZ>
 struct Geo {
@@ -52,7 +53,7 @@ __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n
 // Byte offsets of the shared-memory arrays (16-byte aligned each); the same
 // function sizes the launch on the host.
 struct SpecSmem {
-  size_t twr, ring, xc, pbuf, hg, wres, cph, off, total;
+  size_t twr, ring, xc, pbuf, hg, wres, cph, off, dbuf, total;
 };
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
@@ -75,6 +76,7 @@ __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
   L.wres = o; o = align16(o + sizeof(float2) * M);
   L.cph = o;  o = align16(o + sizeof(float2) * M);
   L.off = o;  o = align16(o + sizeof(float2) * npl);
+  L.dbuf = o; o = align16(o + sizeof(float2) * size_t(npl) * tw);
   L.total = o;
   return L;
 }
@@ -127,15 +129,14 @@ __device__ __forceinline__ void observer_hann(const float* pa, const float2* lam
 }
 
 template <int M, int MZ>
-__global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const SpecArgs a) {
+__global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const SpecArgs a) {
   using G = Geo<M, MZ>;
   constexpr int K = G::K, J = G::J, NPL = G::NPL;
   constexpr bool EVEN = G::EVEN;
   const SpecTables& tb = *a.tables;
-  const int TW = a.tw, TH = a.th, H = a.H, W = a.W;
+  const int TW = a.tw, H = a.H, W = a.W;
   const int RW = TW + 2 * K;
   const int nch = tb.nch, nchy = tb.nchy, nh = tb.nh, nslot = tb.nslot;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int PS = (nchy * M) | 1;                          // odd pixel stride of pbuf
 
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
   float2* wres = reinterpret_cast<float2*>(smem_raw + SL.wres);       // [M]
   float2* cph = reinterpret_cast<float2*>(smem_raw + SL.cph);         // [M]
   float2* offs = reinterpret_cast<float2*>(smem_raw + SL.off);        // [NPL]
+  float2* dbuf = reinterpret_cast<float2*>(smem_raw + SL.dbuf);       // [NPL][TW]
 
   for (int i = tid; i < nch * M; i += nthr) xc[i] = tb.xcoef[i / M][i % M];
   for (int i = tid; i < (nh + 1) * nslot; i += nthr) hg[i] = a.hgather[i];
@@ -156,181 +158,231 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 1) spectrum_kernel(const Spec
   float2 lam[NPL];
 #pragma unroll
   for (int p = 0; p < NPL; ++p) lam[p] = tb.lam[p];
-
   const float2 hz = tb.hann_z;
   const float alpha = a.alpha, oma = 1.0f - alpha;
   const float sP = float(MZ) * float(MZ) / float(M * M * MZ);   // (Mz/sqrt(N))^2
 
-  // ---- phase-C ownership: one (channel, column) per thread --------------------
+  // ---- static task assignment (identical for every row) -----------------------
+  // B: (channel, column) x-DFT tasks, packed: c | x << 8 | plane << 16 | real << 20 | dc << 21
+  int btask[kMaxBTasks];
+#pragma unroll
+  for (int q = 0; q < kMaxBTasks; ++q) {
+    const int task = tid + q * nthr;
+    if (task < nch * TW) {
+      const int c = task / TW, x = task % TW, p = tb.ch_plane[c];
+      const int real = (p == 0) || (EVEN && p == NPL - 1);
+      btask[q] = c | (x << 8) | (p << 16) | (real << 20) | (int(c >= nchy) << 21);
+    } else {
+      btask[q] = -1;
+    }
+  }
+  // C: one (channel, column) y-SDFT per thread
   const bool yth = tid < TW * nchy;
   const int cy = yth ? tid / TW : 0;
   const int xy = yth ? tid % TW : 0;
   const int kxc = tb.ch_kx[cy];
   const int plc = tb.ch_plane[cy];
-  const int dcch = nchy + plc;                           // this plane's box-sum channel
-  float2 Y[M];
+  // D: (pixel column, h) reduction tasks, packed: hi | x << 16
+  const int ntD = TW * (nh + 1);
+  int dtask[kMaxDTasks];
 #pragma unroll
-  for (int k = 0; k < M; ++k) Y[k] = make_float2(0.f, 0.f);
-
-  // ---- phase-A prefetch (row i = 0) --------------------------------------------
-  float pa[kPrefA];
-  auto loadA = [&](int i) {
-    if (tid < RW) {
-      const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + tid, W);
-      const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
-      pa[0] = __ldg(a.frame + o);
-#pragma unroll
-      for (int f = 0; f < MZ; ++f) pa[1 + f] = __ldg(a.obs_old + f * plane + o);
-    }
-  };
-  loadA(0);
-  // Per-plane offset removed from every Tw of this CTA before the spatial sums.
-  // The high-passed, Hann-windowed spectrum is exactly invariant to a spatially
-  // constant offset per temporal plane (it only feeds the removed kx = ky = 0
-  // bin and the correction that cancels its window leakage), so subtracting
-  // one constant per CTA leaves the result unchanged while keeping the FP32
-  // sums at the scale of the texture instead of the scene's DC level.
-  if (tid == 0) {
-    float2 Tn[NPL], Tw0[NPL];
-    observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
-#pragma unroll
-    for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
+  for (int q = 0; q < kMaxDTasks; ++q) {
+    const int task = tid + q * nthr;
+    dtask[q] = task < ntD ? ((task % (nh + 1)) | ((task / (nh + 1)) << 16)) : -1;
   }
 
-  // ---- phase-D prefetch (first output row y0) ----------------------------------
-  const int ntD = TW * (nh + 1);
-  float pdc[kMaxDTasks], pds[kMaxDTasks];
-  auto loadD = [&](int yo) {
+  // ---- this CTA's share of the (strip, row) units -------------------------------
+  const int nstrip = (W + TW - 1) / TW;
+  const long long total = (long long)nstrip * H;
+  const long long u0 = total * blockIdx.x / gridDim.x;
+  const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
+  __syncthreads();
+
+  for (long long u = u0; u < u1;) {
+    const int strip = int(u / H);
+    const int y0 = int(u % H);
+    const int y1 = int(min((long long)H, (long long)y0 + (u1 - u)));
+    u += y1 - y0;
+    const int x0 = strip * TW;
+    const int TH = y1 - y0;
+
+    float2 Y[M];
 #pragma unroll
-    for (int q = 0; q < kMaxDTasks; ++q) {
-      const int task = tid + q * nthr;
-      pdc[q] = 0.f; pds[q] = 0.f;
-      if (task < ntD && yo < H) {
-        const int x = task / (nh + 1), hi = task % (nh + 1);
-        if (x0 + x < W) {
+    for (int k = 0; k < M; ++k) Y[k] = make_float2(0.f, 0.f);
+    float2 drun[kMaxBTasks];
+#pragma unroll
+    for (int q = 0; q < kMaxBTasks; ++q) drun[q] = make_float2(0.f, 0.f);
+
+    // phase-A prefetch of input row 0
+    float pa[kPrefA];
+    auto loadA = [&](int i) {
+      if (tid < RW) {
+        const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + tid, W);
+        const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
+        pa[0] = __ldg(a.frame + o);
+#pragma unroll
+        for (int f = 0; f < MZ; ++f) pa[1 + f] = __ldg(a.obs_old + f * plane + o);
+      }
+    };
+    loadA(0);
+    // Per-plane offset removed from every Tw of this segment before the spatial
+    // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
+    // spatially constant offset per temporal plane (it only feeds the removed
+    // kx = ky = 0 bin and the correction that cancels its window leakage), so
+    // subtracting one constant per segment leaves the result unchanged while
+    // keeping the FP32 sums at the scale of the texture instead of the DC level.
+    if (tid == 0) {
+      float2 Tn[NPL], Tw0[NPL];
+      observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
+    }
+    // phase-D prefetch of the smoother state of the first output row
+    float pdc[kMaxDTasks], pds[kMaxDTasks];
+    auto loadD = [&](int yo) {
+#pragma unroll
+      for (int q = 0; q < kMaxDTasks; ++q) {
+        pdc[q] = 0.f; pds[q] = 0.f;
+        const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
+        if (dtask[q] >= 0 && yo < y1 && x0 + x < W) {
           const float* src = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
           pdc[q] = src[hi];
           if (hi > 0) pds[q] = src[nh + hi];
         }
       }
-    }
-  };
-  loadD(y0);
-  __syncthreads();
-
-  const int nrows = TH + 2 * K;
-  for (int i = 0; i < nrows; ++i) {
-    const int r = y0 - K + i;               // input row (unclamped)
-    // ---------------- A: observer update + Hann along kz ---------------------
-    if (tid < RW) {
-      float2 T[NPL], Tw[NPL];
-      observer_hann<M, MZ>(pa, lam, hz, T, Tw);
-      // owner writes the new state
-      const int xs = x0 - K + tid;
-      if (r >= y0 && r < y0 + TH && r < H && tid >= K && tid < K + TW && xs < W) {
-        const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
-        a.obs_new[o] = T[0].x;
-#pragma unroll
-        for (int j = 1; j <= J; ++j) {
-          a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
-          a.obs_new[(2 * j) * plane + o] = T[j].y;
-        }
-        if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
-      }
-#pragma unroll
-      for (int p = 0; p < NPL; ++p) twr[p * RW + tid] = csub(Tw[p], offs[p]);
-    }
-    if (i + 1 < nrows) loadA(i + 1);
+    };
+    loadD(y0);
     __syncthreads();
 
-    // ---------------- B: x-DFT of the row into the ring ---------------------
-    const int slot = i % (M + 1);
-    for (int task = tid; task < nch * TW; task += nthr) {
-      const int c = task / TW, x = task % TW;
-      const int p = tb.ch_plane[c];
-      const float2* row = twr + p * RW + x + 2 * K;     // u = x + 2K - mx
-      const float2* w = xc + c * M;
-      float2 acc = make_float2(0.f, 0.f);
+    const int nrows = TH + 2 * K;
+    for (int i = 0; i < nrows; ++i) {
+      const int r = y0 - K + i;               // input row (unclamped)
+      // ---------------- A: observer update + Hann along kz -------------------
+      if (tid < RW) {
+        float2 T[NPL], Tw[NPL];
+        observer_hann<M, MZ>(pa, lam, hz, T, Tw);
+        const int xs = x0 - K + tid;
+        if (r >= y0 && r < y1 && tid >= K && tid < K + TW && xs < W) {   // owner writes
+          const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
+          a.obs_new[o] = T[0].x;
 #pragma unroll
-      for (int mx = 0; mx < M; ++mx) {
-        const float2 v = row[-mx], cw = w[mx];
-        acc.x = fmaf(cw.x, v.x, fmaf(-cw.y, v.y, acc.x));
-        acc.y = fmaf(cw.x, v.y, fmaf(cw.y, v.x, acc.y));
-      }
-      ring[(slot * nch + c) * TW + x] = acc;
-    }
-    __syncthreads();
-
-    // ---------------- C: y-SDFT, Hann(ky), high-pass, power -------------------
-    const int yo = r - K;                    // output row of this window
-    const bool outrow = (i >= 2 * K) && (yo < H);
-    if (yth) {
-      const float2 xn = ring[(slot * nch + cy) * TW + xy];
-      float2 d = xn;
-      if (i >= M) d = csub(xn, ring[(((i - M) % (M + 1)) * nch + cy) * TW + xy]);
-#pragma unroll
-      for (int k = 0; k < M; ++k) Y[k] = cadd(cmul(wres[k], Y[k]), cmul(cph[k], d));
-      if (outrow) {
-        // Hann along ky (real taps 1/4, 1/2, 1/4 in the centred basis), minus
-        // Hann_x Hann_y of the removed (0,0) bin, then the power.
-        float2 D = make_float2(0.f, 0.f);
-        float wxh = 0.f;
-        if (kxc >= -1 && kxc <= 1) {
-#pragma unroll
-          for (int my = 0; my < M; ++my) D = cadd(D, ring[((((i - my) % (M + 1)) * nch) + dcch) * TW + xy]);
-          wxh = (kxc == 0) ? 0.5f : 0.25f;
+          for (int j = 1; j <= J; ++j) {
+            a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
+            a.obs_new[(2 * j) * plane + o] = T[j].y;
+          }
+          if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
         }
-        float* pb = pbuf + xy * PS + cy * M;
-        const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          float2 z = cadd(cscale(Y[k], 0.5f), cscale(cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]), 0.25f));
-          if (k == K) z = csub(z, cscale(D, wxh * 0.5f));
-          if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh * 0.25f));
-          const float pw = sP * fmaf(z.x, z.x, z.y * z.y);
-          pb[k] = pw;
-          if (dump) {
-            // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
-            const size_t pix = size_t(yo) * W + x0 + xy;
-            const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
-            const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
-                                     float(MZ) / sqrtf(float(M * M * MZ)));
-            const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
-            const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
-            a.dump_win[op] = sv;
-            a.dump_win[om] = conjf2(sv);
-            if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
+        for (int p = 0; p < NPL; ++p) twr[p * RW + tid] = csub(Tw[p], offs[p]);
+      }
+      if (i + 1 < nrows) loadA(i + 1);
+      __syncthreads();
+
+      // ---------------- B: x-DFT of the row into the ring -------------------
+      const int slot = i % (M + 1);
+      const int oslot = (i + 1) % (M + 1);    // == (i - M) mod (M + 1)
+#pragma unroll
+      for (int q = 0; q < kMaxBTasks; ++q) {
+        const int bt = btask[q];
+        if (bt < 0) continue;
+        const int c = bt & 0xff, x = (bt >> 8) & 0xff, pl = (bt >> 16) & 0xf;
+        const float2* row = twr + pl * RW + x + 2 * K;       // u = x + 2K - mx
+        const float2* w = xc + c * M;
+        float2 acc = make_float2(0.f, 0.f);
+        if (bt & (1 << 20)) {
+#pragma unroll
+          for (int mx = 0; mx < M; ++mx) {
+            const float v = row[-mx].x;
+            const float2 cw = w[mx];
+            acc.x = fmaf(cw.x, v, acc.x);
+            acc.y = fmaf(cw.y, v, acc.y);
+          }
+        } else {
+#pragma unroll
+          for (int mx = 0; mx < M; ++mx) {
+            const float2 v = row[-mx], cw = w[mx];
+            acc.x = fmaf(cw.x, v.x, fmaf(-cw.y, v.y, acc.x));
+            acc.y = fmaf(cw.x, v.y, fmaf(cw.y, v.x, acc.y));
+          }
+        }
+        if (bt & (1 << 21)) {                  // running box sum for the high-pass
+          drun[q] = cadd(drun[q], acc);
+          if (i >= M) drun[q] = csub(drun[q], ring[(oslot * nch + c) * TW + x]);
+          dbuf[pl * TW + x] = drun[q];
+        }
+        ring[(slot * nch + c) * TW + x] = acc;
+      }
+      __syncthreads();
+
+      // ---------------- C: y-SDFT, Hann(ky), high-pass, power ----------------
+      const int yo = r - K;                    // output row of this window
+      const bool outrow = (i >= 2 * K) && (yo < y1);
+      if (yth) {
+        const float2 xn = ring[(slot * nch + cy) * TW + xy];
+        float2 d = xn;
+        if (i >= M) d = csub(xn, ring[(oslot * nch + cy) * TW + xy]);
+#pragma unroll
+        for (int k = 0; k < M; ++k) Y[k] = cadd(cmul(wres[k], Y[k]), cmul(cph[k], d));
+        if (outrow) {
+          // Hann along ky (real taps 1/4, 1/2, 1/4 in the centred basis), minus
+          // Hann_x Hann_y of the removed (0,0) bin, then the power.
+          float2 D = make_float2(0.f, 0.f);
+          float wxh = 0.f;
+          if (kxc >= -1 && kxc <= 1) {
+            D = dbuf[plc * TW + xy];
+            wxh = (kxc == 0) ? 0.5f : 0.25f;
+          }
+          float* pb = pbuf + xy * PS + cy * M;
+          const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            float2 z = cadd(cscale(Y[k], 0.5f), cscale(cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]), 0.25f));
+            if (k == K) z = csub(z, cscale(D, wxh * 0.5f));
+            if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh * 0.25f));
+            const float pw = sP * fmaf(z.x, z.x, z.y * z.y);
+            pb[k] = pw;
+            if (dump) {
+              // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
+              const size_t pix = size_t(yo) * W + x0 + xy;
+              const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
+              const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
+                                       float(MZ) / sqrtf(float(M * M * MZ)));
+              const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
+              const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
+              a.dump_win[op] = sv;
+              a.dump_win[om] = conjf2(sv);
+              if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
+            }
           }
         }
       }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // ---------------- D: reduce over kz, smooth, store -----------------------
-    if (outrow) {
+      // ---------------- D: reduce over kz, smooth, store ---------------------
+      if (outrow) {
 #pragma unroll
-      for (int q = 0; q < kMaxDTasks; ++q) {
-        const int task = tid + q * nthr;
-        if (task >= ntD) break;
-        const int x = task / (nh + 1), hi = task % (nh + 1);
-        if (x0 + x >= W) continue;
-        const int* g = hg + hi * nslot;
-        const float* pb = pbuf + x * PS;
-        float Ac = pb[g[0]], As = 0.f;
+        for (int q = 0; q < kMaxDTasks; ++q) {
+          const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
+          if (dtask[q] < 0 || x0 + x >= W) continue;
+          const int* g = hg + hi * nslot;
+          const float* pb = pbuf + x * PS;
+          float Ac = pb[g[0]], As = 0.f;
 #pragma unroll
-        for (int j = 1; j <= J; ++j) {
-          const float pp = pb[g[j]], pm = pb[g[J + j]];
-          Ac = fmaf(pp + pm, tb.cz[j], Ac);
-          As = fmaf(pp - pm, tb.sz[j], As);
+          for (int j = 1; j <= J; ++j) {
+            const float pp = pb[g[j]], pm = pb[g[J + j]];
+            Ac = fmaf(pp + pm, tb.cz[j], Ac);
+            As = fmaf(pp - pm, tb.sz[j], As);
+          }
+          if (EVEN) Ac -= pb[g[2 * J + 1]];
+          float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
+          dst[hi] = fmaf(oma, Ac, alpha * pdc[q]);
+          if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * pds[q]);
         }
-        if (EVEN) Ac -= pb[g[2 * J + 1]];
-        float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-        dst[hi] = fmaf(oma, Ac, alpha * pdc[q]);
-        if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * pds[q]);
+        loadD(yo + 1);
       }
-      loadD(yo + 1);
+      // pbuf, dbuf and the ring slot are rewritten only after the next barriers
     }
-    // pbuf and the ring slot are rewritten only after the next two barriers
+    __syncthreads();   // before the next segment rewrites offs
   }
 }
 
@@ -353,8 +405,17 @@ static cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   auto kern = spectrum_kernel<M, MZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem));
   if (e != cudaSuccess) return e;
-  dim3 grid((a.W + a.tw - 1) / a.tw, (a.H + a.th - 1) / a.th);
-  kern<<<grid, L.threads, L.smem, st>>>(a);
+  int dev = 0, nsm = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.threads, L.smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // one wave of CTAs, each with an equal share of the (strip, row) units
+  const long long units = (long long)((a.W + a.tw - 1) / a.tw) * a.H;
+  long long grid = (long long)nsm * per_sm;
+  if (grid > units) grid = units;
+  kern<<<unsigned(grid), L.threads, L.smem, st>>>(a);
   return cudaGetLastError();
 }
 

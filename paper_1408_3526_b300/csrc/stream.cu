@@ -153,7 +153,7 @@ static int pick_tile_w(int M, int Mz) {
   const int K = (M - 1) / 2, J = (Mz - 1) / 2;
   const bool even = (Mz % 2) == 0;
   const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
-  int tw = 768 / nchy;
+  int tw = 384 / nchy;         // <= 384 threads: two CTAs per SM
   if (tw > 32) tw = 32;
   if (tw < 1) tw = 1;
   return tw;
@@ -289,7 +289,10 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     }
   // the phase-D task split must fit the kernel's per-thread budget
   const int nthr = spectrum_threads(M, Mz, s->tw);
-  if (s->tw * ((M * M - 1) / 2 + 1) > 4 * nthr || spectrum_smem(M, Mz, s->tw) > 227 * 1024) {
+  const int nreal = 1 + (Mz % 2 == 0 ? 1 : 0), npl = (Mz - 1) / 2 + nreal;
+  const int nch_all = nreal * ((M - 1) / 2 + 1) + ((Mz - 1) / 2) * M + npl;
+  if (s->tw * ((M * M - 1) / 2 + 1) > 4 * nthr || s->tw * nch_all > 2 * nthr ||
+      spectrum_smem(M, Mz, s->tw) > 227 * 1024) {
     free_stream(s);
     return WH_EUNSUP;
   }
