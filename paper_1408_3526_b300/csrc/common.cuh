@@ -97,5 +97,6 @@ cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st);
 cudaError_t launch_pef(const PefArgs& a, cudaStream_t st);
 cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
 bool spectrum_supported(int M, int Mz);
+cudaError_t spectrum_init_constants();
 
 }  // namespace wh

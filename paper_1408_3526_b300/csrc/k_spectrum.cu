@@ -29,6 +29,8 @@
 //   D  per output pixel, reduce P over kz into A, smooth, store.
 // Register prefetch hides the HBM latency of the next row's frame/observer
 // state (phase A) and of the next output row's smoother state (phase D).
+#include <cmath>
+
 #include "common.cuh"
 
 namespace wh {
@@ -50,10 +52,31 @@ struct Geo {
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
+// Resonator twiddles e^{+j2pi ky/M} and centring phases e^{-j2pi ky K/M} per
+// window size (index (M-3)/2, ky+K); indexed at compile time in the kernel, so
+// they are read as constant-bank operands.
+__constant__ float2 c_wres[7][kMaxM];
+__constant__ float2 c_cph[7][kMaxM];
+
+// Per-thread asynchronous 4-byte copies global -> shared (each thread later
+// consumes only what it copied, so a wait on its own groups suffices).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__host__ __device__ inline int spec_threads_for(int M, int Mz, int tw) {
+  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
+  const int nchy = (1 + ((Mz % 2) == 0 ? 1 : 0)) * (K + 1) + J * M;
+  return ((tw * nchy + 31) / 32) * 32;
+}
+
 // Byte offsets of the shared-memory arrays (16-byte aligned each); the same
 // function sizes the launch on the host.
 struct SpecSmem {
-  size_t twr, ring, xc, pbuf, hg, wres, cph, off, dbuf, total;
+  size_t twr, ring, xc, pbuf, hg, wres, cph, off, dbuf, abuf, dpre, total;
 };
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
@@ -77,6 +100,8 @@ __host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
   L.cph = o;  o = align16(o + sizeof(float2) * M);
   L.off = o;  o = align16(o + sizeof(float2) * npl);
   L.dbuf = o; o = align16(o + sizeof(float2) * size_t(npl) * tw);
+  L.abuf = o; o = align16(o + sizeof(float) * size_t(RW) * kPrefA);
+  L.dpre = o; o = align16(o + sizeof(float) * size_t(kMaxDTasks) * 2 * spec_threads_for(M, Mz, tw));
   L.total = o;
   return L;
 }
@@ -147,14 +172,14 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
   float2* xc = reinterpret_cast<float2*>(smem_raw + SL.xc);           // [nch][M]
   float* pbuf = reinterpret_cast<float*>(smem_raw + SL.pbuf);         // [TW][PS]
   int* hg = reinterpret_cast<int*>(smem_raw + SL.hg);                 // [(nh+1)][nslot]
-  float2* wres = reinterpret_cast<float2*>(smem_raw + SL.wres);       // [M]
-  float2* cph = reinterpret_cast<float2*>(smem_raw + SL.cph);         // [M]
   float2* offs = reinterpret_cast<float2*>(smem_raw + SL.off);        // [NPL]
   float2* dbuf = reinterpret_cast<float2*>(smem_raw + SL.dbuf);       // [NPL][TW]
+  float* abuf = reinterpret_cast<float*>(smem_raw + SL.abuf);         // [RW][kPrefA]
+  float* dpre = reinterpret_cast<float*>(smem_raw + SL.dpre);         // [kMaxDTasks][2][nthr]
+  constexpr int MI = (M - 3) / 2;
 
   for (int i = tid; i < nch * M; i += nthr) xc[i] = tb.xcoef[i / M][i % M];
   for (int i = tid; i < (nh + 1) * nslot; i += nthr) hg[i] = a.hgather[i];
-  for (int i = tid; i < M; i += nthr) { wres[i] = tb.wres[i]; cph[i] = tb.cphase[i]; }
   float2 lam[NPL];
 #pragma unroll
   for (int p = 0; p < NPL; ++p) lam[p] = tb.lam[p];
@@ -213,18 +238,27 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
 #pragma unroll
     for (int q = 0; q < kMaxBTasks; ++q) drun[q] = make_float2(0.f, 0.f);
 
-    // phase-A prefetch of input row 0
-    float pa[kPrefA];
+    // phase-A prefetch of input row i into this thread's slot of abuf
     auto loadA = [&](int i) {
       if (tid < RW) {
         const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + tid, W);
         const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
-        pa[0] = __ldg(a.frame + o);
+        float* dst = abuf + tid * kPrefA;
+        cp_async4(dst, a.frame + o);
 #pragma unroll
-        for (int f = 0; f < MZ; ++f) pa[1 + f] = __ldg(a.obs_old + f * plane + o);
+        for (int f = 0; f < MZ; ++f) cp_async4(dst + 1 + f, a.obs_old + f * plane + o);
       }
+      cp_async_commit();
     };
     loadA(0);
+    float pa[kPrefA];
+    auto readA = [&]() {
+      cp_async_wait1();
+      if (tid < RW) {
+#pragma unroll
+        for (int f = 0; f <= MZ; ++f) pa[f] = abuf[tid * kPrefA + f];
+      }
+    };
     // Per-plane offset removed from every Tw of this segment before the spatial
     // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
     // spatially constant offset per temporal plane (it only feeds the removed
@@ -232,24 +266,25 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     // subtracting one constant per segment leaves the result unchanged while
     // keeping the FP32 sums at the scale of the texture instead of the DC level.
     if (tid == 0) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[f];
       float2 Tn[NPL], Tw0[NPL];
       observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
     }
-    // phase-D prefetch of the smoother state of the first output row
-    float pdc[kMaxDTasks], pds[kMaxDTasks];
+    // phase-D prefetch of the smoother state of an output row (own slots of dpre)
     auto loadD = [&](int yo) {
 #pragma unroll
       for (int q = 0; q < kMaxDTasks; ++q) {
-        pdc[q] = 0.f; pds[q] = 0.f;
         const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
         if (dtask[q] >= 0 && yo < y1 && x0 + x < W) {
           const float* src = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-          pdc[q] = src[hi];
-          if (hi > 0) pds[q] = src[nh + hi];
+          cp_async4(dpre + (q * 2 + 0) * nthr + tid, src + hi);
+          if (hi > 0) cp_async4(dpre + (q * 2 + 1) * nthr + tid, src + nh + hi);
         }
       }
+      cp_async_commit();
     };
     loadD(y0);
     __syncthreads();
@@ -258,6 +293,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     for (int i = 0; i < nrows; ++i) {
       const int r = y0 - K + i;               // input row (unclamped)
       // ---------------- A: observer update + Hann along kz -------------------
+      readA();
       if (tid < RW) {
         float2 T[NPL], Tw[NPL];
         observer_hann<M, MZ>(pa, lam, hz, T, Tw);
@@ -276,6 +312,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
         for (int p = 0; p < NPL; ++p) twr[p * RW + tid] = csub(Tw[p], offs[p]);
       }
       if (i + 1 < nrows) loadA(i + 1);
+      else cp_async_commit();
       __syncthreads();
 
       // ---------------- B: x-DFT of the row into the ring -------------------
@@ -322,7 +359,11 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
         float2 d = xn;
         if (i >= M) d = csub(xn, ring[(oslot * nch + cy) * TW + xy]);
 #pragma unroll
-        for (int k = 0; k < M; ++k) Y[k] = cadd(cmul(wres[k], Y[k]), cmul(cph[k], d));
+        for (int k = 0; k < M; ++k) {
+          const float2 w = c_wres[MI][k], c = c_cph[MI][k];
+          Y[k] = make_float2(fmaf(w.x, Y[k].x, fmaf(-w.y, Y[k].y, fmaf(c.x, d.x, -c.y * d.y))),
+                             fmaf(w.x, Y[k].y, fmaf(w.y, Y[k].x, fmaf(c.x, d.y, c.y * d.x))));
+        }
         if (outrow) {
           // Hann along ky (real taps 1/4, 1/2, 1/4 in the centred basis), minus
           // Hann_x Hann_y of the removed (0,0) bin, then the power.
@@ -359,6 +400,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
       __syncthreads();
 
       // ---------------- D: reduce over kz, smooth, store ---------------------
+      cp_async_wait1();
       if (outrow) {
 #pragma unroll
         for (int q = 0; q < kMaxDTasks; ++q) {
@@ -375,13 +417,16 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
           }
           if (EVEN) Ac -= pb[g[2 * J + 1]];
           float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-          dst[hi] = fmaf(oma, Ac, alpha * pdc[q]);
-          if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * pds[q]);
+          dst[hi] = fmaf(oma, Ac, alpha * dpre[(q * 2 + 0) * nthr + tid]);
+          if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * dpre[(q * 2 + 1) * nthr + tid]);
         }
         loadD(yo + 1);
+      } else {
+        cp_async_commit();
       }
       // pbuf, dbuf and the ring slot are rewritten only after the next barriers
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();   // before the next segment rewrites offs
   }
 }
@@ -424,6 +469,28 @@ static cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   X(7, 3) X(7, 4) X(7, 5) X(7, 6) \
   X(9, 3) X(9, 4) X(9, 5) X(9, 6) \
   X(15, 4) X(15, 5) X(15, 6)
+
+// Upload the constant twiddle tables for window M (all sizes at once, per device).
+cudaError_t spectrum_init_constants() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && done[dev]) return cudaSuccess;
+  float2 w[7][kMaxM], c[7][kMaxM];
+  for (int mi = 0; mi < 7; ++mi) {
+    const int M = 2 * mi + 3, K = (M - 1) / 2;
+    for (int i = 0; i < kMaxM; ++i) {
+      const int k = i - K;
+      const double pi = 3.14159265358979323846;
+      w[mi][i] = make_float2(float(std::cos(2 * pi * k / M)), float(std::sin(2 * pi * k / M)));
+      c[mi][i] = make_float2(float(std::cos(-2 * pi * k * K / M)), float(std::sin(-2 * pi * k * K / M)));
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_wres, w, sizeof(w));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cph, c, sizeof(c));
+  if (e == cudaSuccess && dev < 64) done[dev] = true;
+  return e;
+}
 
 bool spectrum_supported(int M, int Mz) {
 #define X(m, z) if (M == m && Mz == z) return true;

@@ -246,6 +246,12 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     free_stream(s);
     return rc;
   }
+  e = spectrum_init_constants();
+  if (e != cudaSuccess) {
+    int rc = set_cuda_err(e, "cudaMemcpyToSymbol");
+    free_stream(s);
+    return rc;
+  }
   // tables
   SpecTables tb;
   std::vector<int> hg;
