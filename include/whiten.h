@@ -166,6 +166,31 @@ int wh_output_pointers(wh_stream *s, float **whitened, float **vx, float **vy, i
 int wh_profile_enable(wh_stream *s, int on);
 int wh_profile_read(wh_stream *s, double *ms, long long *n, int reset);
 
+/*
+ * Tensor-core GEMM (tcgen05, F32 accumulation in tensor memory):
+ *   C[M][N] = A[M][K] * B[N][K]^T (+ bias[N]) (then GELU if gelu = 1),
+ * A and B row-major with K contiguous (leading dimensions lda, ldb >= K,
+ * rows 16-byte aligned), both F16 (bf16 = 0) or both BF16 (bf16 = 1).  C is
+ * float32 (out_bf16 = 0) or BF16 (out_bf16 = 1) with leading dimension ldc.
+ * All pointers are device pointers; the call runs on cuda_stream and
+ * synchronises it to read the kernel's error flag.  This is the contraction
+ * engine of the learned velocity estimator and of the tensor-core
+ * autocorrelation (Eq. (10) as [pixels x bins] x [bins x grid]).
+ * Errors: WH_EINVAL (shapes, alignment), WH_ETIMEOUT (a bounded device wait ran
+ * out), WH_ECUDA.
+ */
+int wh_tc_gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc, int M, int N, int K,
+               int bf16, int out_bf16, const float *bias, int gelu, void *cuda_stream);
+
+/*
+ * Same contraction with a row-wise selection epilogue: for every row of C and
+ * every 128-column tile, the 4 largest values among the first n_valid columns
+ * (ties to the lowest column), written to cand_val/cand_idx[M][ceil(N/128)][4]
+ * (device pointers).  Used to shortlist autocorrelation peaks.
+ */
+int wh_tc_gemm_topk(const void *A, int lda, const void *B, int ldb, int M, int N, int K, int bf16,
+                    int n_valid, float *cand_val, int *cand_idx, void *cuda_stream);
+
 /* Reset the recursive state to zero (as if no frame had been pushed). */
 int wh_reset_stream(wh_stream *s);
 

@@ -69,6 +69,10 @@ _SIGS = {
                                      C.POINTER(_VP)]),
     "wh_profile_enable": (C.c_int, [_VP, C.c_int]),
     "wh_profile_read": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
+    "wh_tc_gemm": (C.c_int, [_VP, C.c_int, _VP, C.c_int, _VP, C.c_int, C.c_int, C.c_int, C.c_int,
+                             C.c_int, C.c_int, _VP, C.c_int, _VP]),
+    "wh_tc_gemm_topk": (C.c_int, [_VP, C.c_int, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_int, _VP, _VP, _VP]),
     "wh_reset_stream": (C.c_int, [_VP]),
     "wh_destroy_stream": (C.c_int, [_VP]),
     "wh_status_string": (C.c_char_p, [C.c_int]),

@@ -1,0 +1,70 @@
+// C ABI of the tensor-core GEMM (used by the learned velocity estimator and
+// the autocorrelation contraction; exported for direct use and testing).
+#include <cstdio>
+
+#include "../../include/whiten.h"
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+using namespace wh;
+
+namespace {
+thread_local char g_err2[256] = "";
+int* device_err_flag() {
+  static int* flags[64] = {nullptr};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!flags[dev]) {
+    if (cudaMalloc(&flags[dev], sizeof(int)) != cudaSuccess) return nullptr;
+    cudaMemset(flags[dev], 0, sizeof(int));
+  }
+  return flags[dev];
+}
+}  // namespace
+
+extern "C" int wh_tc_gemm(const void* A, int lda, const void* B, int ldb, void* C, int ldc, int M, int N,
+                          int K, int bf16, int out_bf16, const float* bias, int gelu, void* cuda_stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N) return WH_EINVAL;
+  int* err = device_err_flag();
+  if (!err) return WH_ENOMEM;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.bf16 = bf16 ? 1 : 0;
+  g.epi = out_bf16 ? EPI_BF16 : EPI_F32; g.act = gelu ? 1 : 0; g.bias = bias;
+  g.C = C; g.ldc = ldc; g.err = err;
+  const int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  cudaError_t e = tc_gemm(g, A, lda, B, ldb, bn, st);
+  if (e != cudaSuccess) return WH_EINVAL;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return WH_ECUDA;
+  if (h) {
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    return WH_ETIMEOUT;
+  }
+  return WH_OK;
+}
+
+extern "C" int wh_tc_gemm_topk(const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                               int bf16, int n_valid, float* cand_val, int* cand_idx, void* cuda_stream) {
+  if (!A || !B || !cand_val || !cand_idx || M < 1 || N < 1 || K < 1) return WH_EINVAL;
+  int* err = device_err_flag();
+  if (!err) return WH_ENOMEM;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.bf16 = bf16 ? 1 : 0; g.epi = EPI_TOPK;
+  g.cand_val = cand_val; g.cand_idx = cand_idx; g.n_valid = n_valid; g.err = err;
+  cudaError_t e = tc_gemm(g, A, lda, B, ldb, 128, st);
+  if (e != cudaSuccess) return WH_EINVAL;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return WH_ECUDA;
+  if (h) {
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    return WH_ETIMEOUT;
+  }
+  return WH_OK;
+}

@@ -1,0 +1,244 @@
+// Tensor-core GEMM on tcgen05 (sm_103a): C[M x N] = A[M x K] * B[N x K]^T
+// with F16 or BF16 operands (both K-major in HBM), F32 accumulation in TMEM.
+//
+// One CTA computes a 128 x BN tile.  Warp roles:
+//   warp 0  TMA producer (one lane): A and B 64-wide K blocks into a 4-stage
+//           ring of 128-byte-swizzled shared-memory tiles (mbarrier full/empty)
+//   warp 1  MMA issuer (one lane): 4 x tcgen05.mma (K = 16 each) per K block,
+//           tcgen05.commit frees the stage; a final commit signals the epilogue
+//   warps 2-5  epilogue: tcgen05.ld of their 32-lane TMEM quadrant, 32 columns
+//           at a time, then the selected epilogue.
+// Every wait is bounded (about one second); on timeout the CTA records an
+// error code in *err, stops issuing work, and still frees its TMEM.
+//
+// Epilogues:
+//   EPI_F32    C (float) = acc (+ bias[col]) (GELU if act)
+//   EPI_BF16   C (bf16)  = GELU?(acc + bias[col]); optional pre-activation (float)
+//   EPI_TOPK   per row, the 4 largest columns (value, index) of this N tile among
+//              the first n_valid columns, ties to the lowest index, written to
+//              cand_val/cand_idx[row][tile][4]
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace wh {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;          // 64 two-byte elements = one 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ float gelu_tanh(float x) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  return 0.5f * x * (1.f + tanhf(k0 * (x + k1 * x * x * x)));
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base_u32 = tc::smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+  uint8_t* sA = smem;                                    // kStages x 16 KB
+  uint8_t* sB = smem + kStages * kBM * kBK * 2;          // kStages x BN*128 B
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * BN * kBK * 2);
+  uint64_t* empty = full + kStages;
+  uint64_t* accum = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int nk = (g.K + kBK - 1) / kBK;
+  constexpr uint32_t kStageBytes = (kBM + BN) * kBK * 2;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < kStages; ++s) {
+        tc::mbar_init(&full[s], 1);
+        tc::mbar_init(&empty[s], 1);
+      }
+      tc::mbar_init(accum, 1);
+      *abort_flag = 0;
+      tc::fence_mbar_init();
+      tc::tma_prefetch_desc(&tmA);
+      tc::tma_prefetch_desc(&tmB);
+    }
+    __syncwarp();
+    tc::tmem_alloc(tmem_slot, BN);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t use = kb / kStages;
+      if (kb >= kStages && !tc::mbar_wait(&empty[s], (use & 1) ^ 1, kWaitNs)) {
+        atomicExch(g.err, 1);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      tc::mbar_expect_tx(&full[s], kStageBytes);
+      tc::tma_load_2d(sA + s * kBM * kBK * 2, &tmA, &full[s], kb * kBK, m0);
+      tc::tma_load_2d(sB + s * BN * kBK * 2, &tmB, &full[s], kb * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = tc::idesc_f16(kBM, BN, g.bf16 != 0);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t use = kb / kStages;
+      if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+        atomicExch(g.err, 2);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + s * kBM * kBK * 2);
+      const uint32_t b0 = tc::smem_u32(sB + s * BN * kBK * 2);
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k) {
+        tc::mma_f16(tmem, tc::sdesc_sw128(a0 + 32 * k), tc::sdesc_sw128(b0 + 32 * k), idesc,
+                    (kb > 0 || k > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    if (ok) tc::mma_commit(accum);
+    else tc::mbar_arrive(accum);          // release the epilogue (it checks the flag)
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;                   // TMEM lane quadrant of this warp
+    const int row = m0 + q * 32 + lane;
+    const bool waited = tc::mbar_wait(accum, 0, 4 * kWaitNs);
+    if (!waited) atomicExch(g.err, 3);
+    tc::tc_fence_after();
+    const bool live = waited && (*abort_flag == 0);
+    float tv[4];
+    int ti[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) { tv[t] = -INFINITY; ti[t] = 0x7fffffff; }
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t r[32];
+      if (live) {
+        tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c * 32), r);
+        tc::tmem_ld_wait();
+      }
+      if (!live || row >= g.M) continue;
+      const int col0 = n0 + c * 32;
+      if (g.epi == EPI_TOPK) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = col0 + j;
+          const float v = __uint_as_float(r[j]);
+          if (col < g.n_valid && v > tv[3]) {
+            // insert keeping descending order (earlier columns win ties)
+            if (v > tv[0]) { tv[3] = tv[2]; ti[3] = ti[2]; tv[2] = tv[1]; ti[2] = ti[1]; tv[1] = tv[0]; ti[1] = ti[0]; tv[0] = v; ti[0] = col; }
+            else if (v > tv[1]) { tv[3] = tv[2]; ti[3] = ti[2]; tv[2] = tv[1]; ti[2] = ti[1]; tv[1] = v; ti[1] = col; }
+            else if (v > tv[2]) { tv[3] = tv[2]; ti[3] = ti[2]; tv[2] = v; ti[2] = col; }
+            else { tv[3] = v; ti[3] = col; }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = col0 + j;
+          if (col >= g.N) break;
+          float v = __uint_as_float(r[j]);
+          if (g.bias) v += g.bias[col];
+          if (g.preact) g.preact[size_t(row) * g.ldp + col] = v;
+          if (g.act) v = gelu_tanh(v);
+          if (g.epi == EPI_F32) reinterpret_cast<float*>(g.C)[size_t(row) * g.ldc + col] = v;
+          else reinterpret_cast<__nv_bfloat16*>(g.C)[size_t(row) * g.ldc + col] = __float2bfloat16(v);
+        }
+      }
+    }
+    if (live && g.epi == EPI_TOPK && row < g.M) {
+      const size_t o = (size_t(row) * gridDim.y + blockIdx.y) * 4;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { g.cand_val[o + t] = tv[t]; g.cand_idx[o + t] = ti[t]; }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, BN);
+  }
+}
+
+// ---- host side: tensor maps through the driver entry point -----------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// K-major [rows][ld] 2-byte matrix, box 64 x box_rows, 128-byte swizzle, OOB -> 0.
+bool make_map(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int box_rows, bool bf16) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((size_t(ld) * 2) & 15)) return false;
+  cuuint64_t gdim[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  cuuint64_t gstride[1] = {cuuint64_t(ld) * 2};
+  cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(ptr), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, g.M, g.K, lda, kBM, g.bf16) || !make_map(&mb, B, g.N, g.K, ldb, BN, g.bf16))
+    return cudaErrorInvalidValue;
+  const size_t smem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 1) * 8 + 16;
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN);
+  tc_gemm_kernel<BN><<<grid, 192, smem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_gemm(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, int bn,
+                    cudaStream_t st) {
+  if (g.M < 1 || g.N < 1 || g.K < 1 || !g.err) return cudaErrorInvalidValue;
+  switch (bn) {
+    case 64: return launch_bn<64>(g, A, lda, B, ldb, st);
+    case 128: return launch_bn<128>(g, A, lda, B, ldb, st);
+    case 256: return launch_bn<256>(g, A, lda, B, ldb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wh

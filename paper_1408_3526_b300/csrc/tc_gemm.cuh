@@ -1,0 +1,30 @@
+// Host interface of the tcgen05 GEMM (see tc_gemm.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace wh {
+
+enum { EPI_F32 = 0, EPI_BF16 = 1, EPI_TOPK = 2 };
+
+struct GemmArgs {
+  int M, N, K;
+  int bf16;             // 1: BF16 operands, 0: F16
+  int epi;              // EPI_*
+  int act;              // 1: GELU (tanh form) after the bias
+  const float* bias;    // [N] or null
+  void* C;              // EPI_F32: float [M][ldc]; EPI_BF16: bf16 [M][ldc]
+  int ldc;
+  float* preact;        // optional float [M][ldp] pre-activation (acc + bias)
+  int ldp;
+  float* cand_val;      // EPI_TOPK: [M][N tiles][4]
+  int* cand_idx;
+  int n_valid;          // EPI_TOPK: columns >= n_valid are ignored
+  int* err;             // device error flag (0 = ok)
+};
+
+// A: [M][lda] K-major, B: [N][ldb] K-major (2-byte elements, 16-byte aligned rows).
+// bn: N tile (64, 128 or 256).
+cudaError_t tc_gemm(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, int bn,
+                    cudaStream_t st);
+
+}  // namespace wh
