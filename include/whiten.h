@@ -51,12 +51,20 @@ extern "C" {
 #define WH_ETIMEOUT  -6   /* a bounded device-side wait ran out (error flag set, no hang) */
 #define WH_EUNSUP    -7   /* parameter combination not built into this library */
 
-/* ---- velocity-estimation and precision modes ---------------------------- */
-#define WH_VEL_PLAIN        0  /* autocorrelation search (Eq. (10)), FP32-exact argmax */
-#define WH_PREC_FP32        0  /* plain form: FP32 recursion, FP32-exact autocorrelation */
-#define WH_PREC_TC_FP16     1  /* autocorrelation contraction on tcgen05, FP16 x FP16 -> FP32 */
-#define WH_PREC_TC_BF16     2  /* autocorrelation contraction on tcgen05, BF16 x BF16 -> FP32 */
-#define WH_PREC_KAHAN       4  /* flag: compensated FP32 sums in the spatial SDFT recursion */
+/* ---- precision / engine of the autocorrelation search ------------------- */
+/* WH_PREC_FP32: FP32 recursion and the exact FP32 argmax of Eq. (10), by the
+ *   separable evaluation on CUDA cores (default), or with WH_PREC_TC_SHORTLIST
+ *   by a tcgen05 F16 contraction that shortlists peaks followed by an FP32
+ *   re-evaluation of every shortlisted grid point within the rigorous F16
+ *   error window (whole grid when the shortlist could be incomplete).
+ * WH_PREC_TC_FP16 / WH_PREC_TC_BF16: precision study, the tensor-core F16 or
+ *   BF16 contraction (F32 accumulation) decides alone.
+ * WH_PREC_CUDA_CORES: accepted for clarity, same as the default. */
+#define WH_PREC_FP32          0
+#define WH_PREC_TC_FP16       1
+#define WH_PREC_TC_BF16       2
+#define WH_PREC_CUDA_CORES    8
+#define WH_PREC_TC_SHORTLIST 16
 
 /* Velocity grid: {-vmax, -vmax + step, ..., +vmax} on both axes
  * (Sec. 3: l_x = l_y = [-8 .. 8]/4, a 17 x 17 grid at vmax = 2, step 1/4).
@@ -149,6 +157,10 @@ int wh_read_autocorr(wh_stream *s, float *out, int is_device);
 /* Grid length L and the output delay m'_z of a stream. */
 int wh_stream_info(const wh_stream *s, int *grid_len, int *delay_z, int *band,
                    long long *frames_pushed);
+
+/* Counters: pixel-frames whose tensor-core shortlist could be incomplete and
+ * were evaluated on the whole grid (WH_PREC_TC_SHORTLIST only; else 0). */
+int wh_stream_stats(wh_stream *s, long long *fallback_pixels);
 
 /* Device pointers of the stream's output buffers (valid until destroy):
  * whitened[h][w], vx[h][w], vy[h][w] (float32), vidx[h][w] (int32).

@@ -25,7 +25,8 @@ WH_EUNSUP = -7
 WH_PREC_FP32 = 0
 WH_PREC_TC_FP16 = 1
 WH_PREC_TC_BF16 = 2
-WH_PREC_KAHAN = 4
+WH_PREC_CUDA_CORES = 8
+WH_PREC_TC_SHORTLIST = 16
 
 WH_SPEC_RAW = 0
 WH_SPEC_WINDOWED = 1
@@ -65,6 +66,7 @@ _SIGS = {
     "wh_read_autocorr": (C.c_int, [_VP, _VP, C.c_int]),
     "wh_stream_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong)]),
+    "wh_stream_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
     "wh_output_pointers": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
                                      C.POINTER(_VP)]),
     "wh_profile_enable": (C.c_int, [_VP, C.c_int]),

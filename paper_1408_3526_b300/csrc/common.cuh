@@ -68,6 +68,25 @@ struct AutocorrArgs {
   const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
 };
 
+struct AutocorrTcArgs {
+  int H, W, M, L, kpad;
+  int kg;                       // leading dimension of a16 and the table (M^2 rounded up to 8)
+  int ntile;                    // 128-column tiles of the grid
+  int mode;                     // 0: exact FP32 re-rank of the shortlist; 1: tensor-core value decides
+  int bf16;
+  float vmax, vstep;
+  const float* Astate;
+  void* a16;                    // [H*W][kg] F16 or BF16
+  float* l1;                    // [H*W] sum |a16|
+  float* cand_val;              // [H*W][ntile][4]
+  int* cand_idx;
+  int* vidx;
+  float* vx;
+  float* vy;
+  const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
+  int* n_fallback;              // optional counter of pixels evaluated on the whole grid
+};
+
 struct PefArgs {
   int H, W, M, Mz, L, mpz;
   const float* obs;             // T_t, just written
@@ -98,5 +117,8 @@ cudaError_t launch_pef(const PefArgs& a, cudaStream_t st);
 cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
 bool spectrum_supported(int M, int Mz);
 cudaError_t spectrum_init_constants();
+bool autocorr_tc_supported(int M);
+cudaError_t launch_autocorr_convert(const AutocorrTcArgs& a, cudaStream_t st);
+cudaError_t launch_autocorr_rerank(const AutocorrTcArgs& a, cudaStream_t st);
 
 }  // namespace wh

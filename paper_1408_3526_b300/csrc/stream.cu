@@ -14,8 +14,12 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/whiten.h"
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 namespace wh {
 int spectrum_threads(int M, int Mz, int tw);
@@ -63,6 +67,15 @@ struct wh_stream {
   float* d_dump_pow;
   float2* d_raw;
   float* d_rs;
+  // tensor-core autocorrelation
+  int use_tc, tc_mode, tc_bf16, kg, ntile;
+  void* d_a16;
+  float* d_l1;
+  float* d_cval;
+  int* d_cidx;
+  void* d_table;
+  int* d_err;
+  int* d_nfb;
   // per-kernel timing (wh_profile_enable)
   int prof;
   std::vector<cudaEvent_t> ev;   // 4 per timed frame
@@ -159,12 +172,21 @@ static int pick_tile_w(int M, int Mz) {
   return tw;
 }
 
+static void fill_tc_args(const wh_stream* s, AutocorrTcArgs& ta) {
+  ta.H = s->H; ta.W = s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad; ta.kg = s->kg;
+  ta.ntile = s->ntile; ta.mode = s->tc_mode; ta.bf16 = s->tc_bf16;
+  ta.vmax = float(s->vmax); ta.vstep = float(s->vstep); ta.Astate = s->Astate;
+  ta.a16 = s->d_a16; ta.l1 = s->d_l1; ta.cand_val = s->d_cval; ta.cand_idx = s->d_cidx;
+  ta.vidx = s->vidx; ta.vx = s->vx; ta.vy = s->vy; ta.tab_x = s->d_tabx; ta.n_fallback = s->d_nfb;
+}
+
 static void free_stream(wh_stream* s) {
   if (!s) return;
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
-                  s->d_dump_pow, s->d_raw, s->d_rs};
+                  s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
+                  s->d_table, s->d_err, s->d_nfb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -205,7 +227,10 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   const int K = (M - 1) / 2;
   if (p.band > K || p.delay_z >= Mz || p.alpha >= 1.0) return WH_EINVAL;
   if (!spectrum_supported(M, Mz)) return WH_EUNSUP;
-  if ((p.precision & ~WH_PREC_KAHAN) != WH_PREC_FP32) return WH_EUNSUP;
+  const int pmode = p.precision & 3;
+  if (p.precision & ~(3 | WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST)) return WH_EUNSUP;
+  if (pmode == 3) return WH_EINVAL;
+  if (pmode != 0 && !autocorr_tc_supported(M)) return WH_EUNSUP;
 
   wh_stream* s = new (std::nothrow) wh_stream();
   if (!s) return WH_ENOMEM;
@@ -214,6 +239,13 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->vidx = nullptr; s->d_spec = nullptr; s->d_hgather = nullptr; s->d_taby = nullptr;
   s->d_tabx = nullptr; s->d_hw = nullptr; s->d_dump_win = nullptr; s->d_dump_pow = nullptr;
   s->d_raw = nullptr; s->d_rs = nullptr; s->prof = 0; s->ev_used = 0; s->t = 0; s->cur = 0;
+  s->d_a16 = nullptr; s->d_l1 = nullptr; s->d_cval = nullptr; s->d_cidx = nullptr;
+  s->d_table = nullptr; s->d_err = nullptr; s->d_nfb = nullptr;
+  s->tc_mode = pmode == 0 ? 0 : 1;
+  s->tc_bf16 = pmode == 2 ? 1 : 0;
+  s->use_tc = (pmode != 0) || ((p.precision & WH_PREC_TC_SHORTLIST) && autocorr_tc_supported(M));
+  s->kg = ((M * M) + 7) & ~7;
+  s->ntile = (L * L + 127) / 128;
   s->H = H; s->W = W; s->M = M; s->K = K; s->Mz = Mz; s->B = p.band; s->mpz = p.delay_z;
   s->L = L; s->precision = p.precision; s->debug = p.debug_dump;
   s->alpha = p.alpha; s->vmax = grid.vmax; s->vstep = grid.step;
@@ -293,6 +325,59 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
       free_stream(s);
       return rc;
     }
+  if (s->use_tc) {
+    alloc((void**)&s->d_a16, 2 * npix * s->kg);
+    alloc((void**)&s->d_l1, sizeof(float) * npix);
+    alloc((void**)&s->d_cval, sizeof(float) * npix * s->ntile * 4);
+    alloc((void**)&s->d_cidx, sizeof(int) * npix * s->ntile * 4);
+    alloc((void**)&s->d_table, 2 * size_t(s->ntile) * 128 * s->kg);
+    alloc((void**)&s->d_err, sizeof(int));
+    alloc((void**)&s->d_nfb, sizeof(int));
+    if (e != cudaSuccess) {
+      int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "cudaMalloc");
+      free_stream(s);
+      return rc;
+    }
+    // B(l, k) in the state's basis: [1, 2 cos a_h(l), -2 sin a_h(l)], a_h(l) =
+    // 2pi (hx lx + hy ly)/M; rows l >= L^2 are zero.
+    const int nh = (M * M - 1) / 2, Np = s->ntile * 128;
+    std::vector<float> tb32(size_t(Np) * s->kg, 0.f);
+    std::vector<int> hx(nh + 1), hyv(nh + 1);
+    int hi = 1;
+    for (int ky = 1; ky <= K; ++ky) { hx[hi] = 0; hyv[hi] = ky; ++hi; }
+    for (int kx = 1; kx <= K; ++kx)
+      for (int ky = -K; ky <= K; ++ky) { hx[hi] = kx; hyv[hi] = ky; ++hi; }
+    for (int g = 0; g < L * L; ++g) {
+      const double lx = -s->vmax + (g % L) * s->vstep, ly = -s->vmax + (g / L) * s->vstep;
+      float* row = &tb32[size_t(g) * s->kg];
+      row[0] = 1.f;
+      for (int h = 1; h <= nh; ++h) {
+        const double ph = 2.0 * kPi * (hx[h] * lx + hyv[h] * ly) / M;
+        row[h] = float(2.0 * std::cos(ph));
+        row[nh + h] = float(-2.0 * std::sin(ph));
+      }
+    }
+    std::vector<uint16_t> tb16(tb32.size());
+    for (size_t i = 0; i < tb32.size(); ++i) {
+      if (s->tc_bf16) {
+        __nv_bfloat16 b = __float2bfloat16(tb32[i]);
+        std::memcpy(&tb16[i], &b, 2);
+      } else {
+        __half h = __float2half(tb32[i]);
+        std::memcpy(&tb16[i], &h, 2);
+      }
+    }
+    cudaError_t c6 = cudaMemcpy(s->d_table, tb16.data(), 2 * tb16.size(), cudaMemcpyHostToDevice);
+    cudaError_t c7 = cudaMemset(s->d_err, 0, sizeof(int));
+    cudaError_t c8 = cudaMemset(s->d_nfb, 0, sizeof(int));
+    cudaError_t c9 = cudaMemset(s->d_a16, 0, 2 * npix * s->kg);
+    for (cudaError_t c : {c6, c7, c8, c9})
+      if (c != cudaSuccess) {
+        int rc = set_cuda_err(c, "tensor-core tables");
+        free_stream(s);
+        return rc;
+      }
+  }
   // the phase-D task split must fit the kernel's per-thread budget
   const int nthr = spectrum_threads(M, Mz, s->tw);
   const int nreal = 1 + (Mz % 2 == 0 ? 1 : 0), npl = (Mz - 1) / 2 + nreal;
@@ -352,13 +437,30 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   cudaError_t e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
   if (ev) WH_CU(cudaEventRecord(ev[1], s->st));
-  AutocorrArgs aa;
-  aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
-  aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
-  aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
-  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
-  e = launch_autocorr(aa, s->st);
-  if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
+  int nlaunch = 3;
+  if (s->use_tc) {
+    AutocorrTcArgs ta;
+    fill_tc_args(s, ta);
+    e = launch_autocorr_convert(ta, s->st);
+    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation convert kernel");
+    GemmArgs g{};
+    g.M = s->H * s->W; g.N = s->ntile * 128; g.K = s->M * s->M; g.bf16 = s->tc_bf16;
+    g.epi = EPI_TOPK; g.cand_val = s->d_cval; g.cand_idx = s->d_cidx; g.n_valid = s->L * s->L;
+    g.err = s->d_err;
+    e = tc_gemm(g, s->d_a16, s->kg, s->d_table, s->kg, 128, s->st);
+    if (e != cudaSuccess) return set_cuda_err(e, "tensor-core autocorrelation");
+    e = launch_autocorr_rerank(ta, s->st);
+    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation re-rank kernel");
+    nlaunch = 5;
+  } else {
+    AutocorrArgs aa;
+    aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
+    aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
+    aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
+    aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
+    e = launch_autocorr(aa, s->st);
+    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
+  }
   if (ev) WH_CU(cudaEventRecord(ev[2], s->st));
   PefArgs pa;
   pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
@@ -366,7 +468,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   e = launch_pef(pa, s->st);
   if (e != cudaSuccess) return set_cuda_err(e, "PEF kernel");
   if (ev) WH_CU(cudaEventRecord(ev[3], s->st));
-  g_launches.fetch_add(3);
+  g_launches.fetch_add(nlaunch);
   s->cur = 1 - s->cur;
   s->t += 1;
   return WH_OK;
@@ -444,6 +546,17 @@ int wh_stream_info(const wh_stream* s, int* grid_len, int* delay_z, int* band,
   if (delay_z) *delay_z = s->mpz;
   if (band) *band = s->B;
   if (frames_pushed) *frames_pushed = s->t;
+  return WH_OK;
+}
+
+int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
+  if (!s) return WH_EINVAL;
+  int h = 0;
+  if (s->d_nfb) {
+    WH_CU(cudaMemcpyAsync(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    WH_CU(cudaStreamSynchronize(s->st));
+  }
+  if (fallback_pixels) *fallback_pixels = h;
   return WH_OK;
 }
 

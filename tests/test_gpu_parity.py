@@ -17,8 +17,10 @@ pytestmark = pytest.mark.gpu
 def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=True, **kw):
     T, H, W = frames.shape
     g = P.run_gpu(frames, M, Mz, vmax, step, spec_frames=spec_frames, debug=debug, **kw)
+    kw = dict(kw)
     o = oracle.Oracle(M, Mz, vmax, step, B=kw.get("band"), mpz=kw.get("delay_z"),
                       alpha=kw.get("alpha"))
+    kw.pop("precision", None)
     ref = o.run(frames, spec_frames=list(spec_frames), spectrum=True, power=debug,
                 autocorr=True, windowed=debug)
     m = {"spec": 0.0, "win": 0.0, "pow": 0.0, "rs": 0.0}
@@ -49,18 +51,21 @@ def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=
     return g, ref
 
 
-def test_parity_config1_full():
-    """64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2 step 1/4 (in full)."""
+@pytest.mark.parametrize("precision", [16, 0], ids=["tc_shortlist_rerank", "cuda_cores"])
+def test_parity_config1_full(precision):
+    """64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2 step 1/4 (in full),
+    with both FP32-exact engines of the autocorrelation search."""
     sc = scenes.config1_scene(T=32)
-    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31))
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), precision=precision)
 
 
-def test_parity_config2_shape_crop():
+@pytest.mark.parametrize("precision", [16, 0], ids=["tc_shortlist_rerank", "cuda_cores"])
+def test_parity_config2_shape_crop(precision):
     """15 x 15 window, order 6, grid +-3 step 1/4 on a 40 x 56 crop of the
     non-uniform-flow scene (several tiles, ragged tail)."""
     sc = scenes.config2_scene(T=14, H=512, W=640)
     fr = np.ascontiguousarray(sc.frames[:, 200:240, 300:356])
-    _compare(fr, 15, 6, 3.0, 0.25, spec_frames=(13,))
+    _compare(fr, 15, 6, 3.0, 0.25, spec_frames=(13,), precision=precision)
 
 
 @pytest.mark.parametrize("M,Mz,H,W", [(7, 5, 37, 53), (5, 3, 33, 70), (9, 6, 19, 41)])

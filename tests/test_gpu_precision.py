@@ -1,0 +1,101 @@
+"""Precision study (needs a B300): the autocorrelation contraction in F16 and
+BF16 on tensor cores, and the FP32-exact engines, against the FP64 oracle.
+
+1024 x 1280 frames of the uniform-flow scene generator, 15 x 15 window,
+temporal order 6, velocity grid +-2 step 1/4.  Reported per output:
+  spectrum  per-pixel max |S - S_ref| / RMS |S_ref| (crop run, 40 frames)
+  velocity  grid-index agreement and max grid-step distance (sampled pixels,
+            every frame, 500 frames: shows whether the error grows)
+  whitened  max |E - E_ref| / input RMS, with E_ref computed for the same
+            velocity field, first and second half of the sequence
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1408_3526_b300 import _abi, scenes
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+M, MZ, VMAX, VSTEP = 15, 6, 2.0, 0.25
+MODES = {"fp32_exact_tc": 16, "fp32_cuda_cores": 0, "tc_fp16": 1, "tc_bf16": 2}
+
+
+def _run_full(frames, precision):
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    T, H, W = frames.shape
+    vel = np.zeros((T, H, W), np.int16)
+    white = np.zeros((T, H, W), np.float32)
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, precision=precision) as s:
+        buf = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        for t in range(T):
+            buf.copy_(torch.from_numpy(frames[t]))
+            s.push(buf)
+            vel[t] = s.read_velocity(device=True)[2].cpu().numpy()
+            if t >= s.delay_z:
+                white[t] = s.read_whitened(device=True)[0].cpu().numpy()
+    return vel, white
+
+
+def test_precision_study_config3():
+    T, H, W = int(os.environ.get("WH_PREC_T", "500")), 1024, 1280
+    sc = scenes.config1_scene(T=T, H=H, W=W, seed=3)
+    fr = sc.frames
+    o = oracle.Oracle(M, MZ, VMAX, VSTEP)
+    rng = np.random.default_rng(11)
+    pts = [(0, 0), (H - 1, W - 1), (512, 640)] + [
+        (int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(13)]
+    refs = {}
+    for (y, x) in pts:
+        refs[(y, x)] = o.run(fr, crop=(y, x, 1, 1))
+    report = {}
+    half = T // 2
+    for name, prec in MODES.items():
+        vel, white = _run_full(fr, prec)
+        same = [[], []]
+        steps = 0
+        werr = [0.0, 0.0]
+        rms = float(np.sqrt(np.mean(fr.astype(np.float64) ** 2)))
+        for (y, x), ref in refs.items():
+            gi = vel[:, y, x].astype(np.int32)
+            ri = ref["vel_index"][:, 0, 0]
+            for hsel, sl in enumerate((slice(1, half), slice(half, T))):
+                same[hsel].append(gi[sl] == ri[sl])
+            d = np.maximum(np.abs(gi % o.L - ri % o.L), np.abs(gi // o.L - ri // o.L))
+            steps = max(steps, int(d[1:].max()))
+            ref2 = o.run(fr, crop=(y, x, 1, 1), vel_override=np.ascontiguousarray(gi.reshape(T, 1, 1)),
+                         velocity=False)
+            e = np.abs(white[:, y, x] - ref2["whitened"][:, 0, 0])
+            werr[0] = max(werr[0], float(np.nanmax(e[o.mpz:half])) / rms)
+            werr[1] = max(werr[1], float(np.nanmax(e[half:])) / rms)
+        report[name] = {
+            "velocity_identical_first_half": float(np.mean(np.concatenate(same[0]))),
+            "velocity_identical_second_half": float(np.mean(np.concatenate(same[1]))),
+            "velocity_max_grid_steps": steps,
+            "whitened_max_err_over_rms_first_half": werr[0],
+            "whitened_max_err_over_rms_second_half": werr[1],
+        }
+    # spectrum error on a crop (the spectrum does not depend on the engine)
+    crop = np.ascontiguousarray(fr[:40, 480:544, 600:680])
+    g = P.run_gpu(crop, M, MZ, VMAX, VSTEP, spec_frames=(39,), debug=True)
+    ref = o.run(crop, spec_frames=[39], spectrum=True, windowed=True)
+    report["spectrum_rel_err"] = P.spectrum_rel_err(g["spectrum"][39], ref["spectrum"][0])
+    report["windowed_spectrum_rel_err"] = P.spectrum_rel_err(g["windowed"][39], ref["windowed"][0])
+    report["frames"] = T
+    report["sampled_pixels"] = len(pts)
+    print("\n[precision] " + json.dumps(report), flush=True)
+    for name in ("fp32_exact_tc", "fp32_cuda_cores"):
+        r = report[name]
+        assert r["velocity_identical_first_half"] >= 0.999
+        assert r["velocity_identical_second_half"] >= 0.999
+        assert r["velocity_max_grid_steps"] <= 1
+        assert r["whitened_max_err_over_rms_second_half"] <= 1e-3
+    for name in ("tc_fp16", "tc_bf16"):
+        assert report[name]["whitened_max_err_over_rms_second_half"] <= 1e-3
+    assert report["spectrum_rel_err"] <= 1e-4
