@@ -118,6 +118,28 @@ int wh_create_stream(int frame_h, int frame_w, int window, int temporal_order,
 int wh_push_frame(wh_stream *s, const float *frame, int is_device);
 
 /*
+ * Allocation-free variant of wh_push_frame.  The paper has no counterpart; it
+ * exists for callers that cannot allocate device memory once streaming has
+ * started (fixed-memory real-time loops, allocation-free pools, hosts that
+ * forbid driver allocations after start-up).  Same arguments, same outputs
+ * (read with wh_read_whitened / wh_read_velocity) and the same FP32-exact
+ * velocity as wh_push_frame; its autocorrelation search always uses the
+ * tensor-core shortlist with exact FP32 re-evaluation, and that search's
+ * scratch lives in one statically sized device array of the library (about
+ * 10.2 MB, held by every GPU that loads the library until the process exits)
+ * instead of memory allocated per call or per stream.  Nothing is allocated.
+ *   Limits: window <= 15 and grid length L <= 25 (WH_EUNSUP otherwise, with a
+ *   message in wh_last_error); frames of any size (processed in chunks).
+ *   Sharing: all calls on a device share the array and leave their contents
+ *   in it; calls that overlap on the GPU (different CUDA streams or host
+ *   threads) race, so serialise them.  Each call clears what must start at 0.
+ *   Set-up: the first call on a device looks up the array's device address;
+ *   make that first call before any stream capture.
+ * Errors: WH_EINVAL, WH_EUNSUP, WH_ECUDA.
+ */
+int wh_push_frame_noalloc(wh_stream *s, const float *frame, int is_device);
+
+/*
  * Whitened (prediction-error) frame E for frame index t - m'_z, where t is
  * the index of the last frame pushed (first frame = 0), written to
  * out[h][w].  *frame_index (may be NULL) receives t - m'_z.

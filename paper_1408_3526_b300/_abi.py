@@ -60,6 +60,7 @@ _SIGS = {
     "wh_create_stream": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid,
                                    C.POINTER(wh_params), _VP, C.POINTER(_VP)]),
     "wh_push_frame": (C.c_int, [_VP, _VP, C.c_int]),
+    "wh_push_frame_noalloc": (C.c_int, [_VP, _VP, C.c_int]),
     "wh_read_whitened": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(C.c_longlong)]),
     "wh_read_velocity": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_longlong)]),
     "wh_read_spectrum": (C.c_int, [_VP, C.c_int, _VP, C.c_int]),

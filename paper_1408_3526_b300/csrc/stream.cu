@@ -19,6 +19,7 @@
 
 #include "../../include/whiten.h"
 #include "common.cuh"
+#include "stream_internal.h"
 #include "tc_gemm.cuh"
 
 namespace wh {
@@ -43,44 +44,10 @@ static int set_cuda_err(cudaError_t e, const char* what) {
 
 static const double kPi = 3.14159265358979323846;
 
-struct wh_stream {
-  int H, W, M, K, Mz, B, mpz, L, precision, debug;
-  double alpha, vmax, vstep;
-  int tw, th, kpad;
-  int device;
-  cudaStream_t st;
-  long long t;          // frames pushed
-  int cur;              // observer buffer holding T_{t-1}
-  float* obs[2];
-  float* Astate;
-  float* frame;
-  float* whitened;
-  float* vx;
-  float* vy;
-  int* vidx;
-  SpecTables* d_spec;
-  int* d_hgather;
-  float2* d_taby;
-  float2* d_tabx;
-  float* d_hw;
-  float2* d_dump_win;
-  float* d_dump_pow;
-  float2* d_raw;
-  float* d_rs;
-  // tensor-core autocorrelation
-  int use_tc, tc_mode, tc_bf16, kg, ntile;
-  void* d_a16;
-  float* d_l1;
-  float* d_cval;
-  int* d_cidx;
-  void* d_table;
-  int* d_err;
-  int* d_nfb;
-  // per-kernel timing (wh_profile_enable)
-  int prof;
-  std::vector<cudaEvent_t> ev;   // 4 per timed frame
-  size_t ev_used;
-};
+char* wh_error_buffer() { return g_err; }
+int wh_cuda_fail(cudaError_t e, const char* what) { return set_cuda_err(e, what); }
+void wh_count_launches(long long n) { g_launches.fetch_add(n); }
+
 
 // ---------------------------------------------------------------------------
 static double dirichlet(int Wd, double w) {   // Eq. (3), limit value at integers
