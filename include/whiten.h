@@ -225,6 +225,56 @@ int wh_tc_gemm(const void *A, int lda, const void *B, int ldb, void *C, int ldc,
 int wh_tc_gemm_topk(const void *A, int lda, const void *B, int ldb, int M, int N, int K, int bf16,
                     int n_valid, float *cand_val, int *cand_idx, void *cuda_stream);
 
+/* ---- learned velocity estimator --------------------------------------------
+ * An MLP n_in -> h1 -> h2 -> n_out (GELU) on each pixel's log-power spectrum
+ * predicts (vx, vy, confidence logit); it is trained on velocities produced by
+ * the plain search and, in a stream's learned mode, replaces the search for
+ * pixels whose confidence reaches a threshold (the rest still run the exact
+ * search).  The paper's method is the plain search (Sec. 2, Eq. (10)); the
+ * network is an addition of this library.  BF16 weights and activations,
+ * FP32 accumulation on tensor cores, FP32 master weights, AdamW.
+ */
+typedef struct wh_mlp wh_mlp;
+
+/* Create with weights drawn U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from 'seed'.
+ * h1, h2 multiples of 8, n_out <= 16 (3 for the velocity head). */
+int wh_mlp_create(int n_in, int h1, int h2, int n_out, unsigned long long seed, void *cuda_stream,
+                  wh_mlp **out);
+int wh_mlp_destroy(wh_mlp *m);
+/* Number of parameters: W1 [h1][n_in], b1, W2 [h2][h1], b2, W3 [n_out][h2], b3. */
+long long wh_mlp_num_params(const wh_mlp *m);
+/* Copy all parameters (in the order above, row-major, float32) to / from a
+ * host buffer of wh_mlp_num_params floats; get_grads copies the gradients of
+ * the last wh_mlp_train_step in the same layout. */
+int wh_mlp_get_params(wh_mlp *m, float *host, long long n);
+int wh_mlp_set_params(wh_mlp *m, const float *host, long long n);
+int wh_mlp_get_grads(wh_mlp *m, float *host, long long n);
+/* Inference: x BF16 [n][ldx] (device, ldx % 8 == 0, columns >= n_in ignored),
+ * y float32 [n][ldy] (device; first n_out columns written; may be NULL). */
+int wh_mlp_forward(wh_mlp *m, const void *x, int ldx, int n, float *y, int ldy);
+/* One training step on n samples (n % 8 == 0): x BF16 [n][ldx], target float
+ * [n][2] velocity labels (device).  Loss = |v - t|^2 + BCE(sigmoid(c), tc) with
+ * tc = 1 when max(|vx-tx|, |vy-ty|) <= vstep.  apply = 0 computes gradients
+ * only; stats (host, 4 floats, may be NULL: then the call does not
+ * synchronise) receives mean loss, mean squared velocity error, mean BCE and
+ * the fraction within one step. */
+int wh_mlp_train_step(wh_mlp *m, const void *x, int ldx, int n, const float *target, float vstep,
+                      float lr, float weight_decay, int apply, float *stats);
+
+/* Per-pixel features for the network: (log2(P(k)/sum_k P(k) + 1e-6) + 10)/10 of the
+ * high-passed, Hann-windowed power of all M*M*Mz bins, order [kz][ky][kx] as
+ * in wh_read_spectrum, BF16 rows of stride *ld (>= M*M*Mz, padding zero).
+ * set_features(1) makes every push write them; read copies the last frame's. */
+int wh_stream_set_features(wh_stream *s, int enable);
+int wh_read_features(wh_stream *s, void *out, int is_device, int *ld);
+/* Learned velocity mode: per frame the network (not owned; must outlive its
+ * use) runs on every pixel; a pixel whose confidence sigmoid(c) >= threshold
+ * takes the network's velocity rounded to the grid, every other pixel runs
+ * the exact autocorrelation search.  mlp = NULL returns to the plain mode. */
+int wh_stream_set_learned(wh_stream *s, wh_mlp *mlp, float conf_threshold);
+/* Frames processed in learned mode and pixel-frames sent to the search. */
+int wh_stream_learned_stats(wh_stream *s, long long *frames, long long *fallback_pixels);
+
 /* Reset the recursive state to zero (as if no frame had been pushed). */
 int wh_reset_stream(wh_stream *s);
 

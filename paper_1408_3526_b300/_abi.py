@@ -76,6 +76,19 @@ _SIGS = {
                              C.c_int, C.c_int, _VP, C.c_int, _VP]),
     "wh_tc_gemm_topk": (C.c_int, [_VP, C.c_int, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, _VP, _VP, _VP]),
+    "wh_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, _VP, C.POINTER(_VP)]),
+    "wh_mlp_destroy": (C.c_int, [_VP]),
+    "wh_mlp_num_params": (C.c_longlong, [_VP]),
+    "wh_mlp_get_params": (C.c_int, [_VP, _VP, C.c_longlong]),
+    "wh_mlp_set_params": (C.c_int, [_VP, _VP, C.c_longlong]),
+    "wh_mlp_get_grads": (C.c_int, [_VP, _VP, C.c_longlong]),
+    "wh_mlp_forward": (C.c_int, [_VP, _VP, C.c_int, C.c_int, _VP, C.c_int]),
+    "wh_mlp_train_step": (C.c_int, [_VP, _VP, C.c_int, C.c_int, _VP, C.c_float, C.c_float, C.c_float,
+                                    C.c_int, _VP]),
+    "wh_stream_set_features": (C.c_int, [_VP, C.c_int]),
+    "wh_read_features": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(C.c_int)]),
+    "wh_stream_set_learned": (C.c_int, [_VP, _VP, C.c_float]),
+    "wh_stream_learned_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "wh_reset_stream": (C.c_int, [_VP]),
     "wh_destroy_stream": (C.c_int, [_VP]),
     "wh_status_string": (C.c_char_p, [C.c_int]),

@@ -54,6 +54,13 @@ struct SpecArgs {
   const int* hgather;           // [nh+1][nslot] offsets (c*M + iy) into a pixel's P block
   float2* dump_win;             // optional [H*W][Mz][M][M]
   float* dump_pow;              // optional [H*W][Mz][M][M]
+  // learned-estimator features (optional): per pixel, (log2(P(k)/sum P + 1e-6) + 10)/10 of
+  // all M*M*Mz bins in the order [kz][ky][kx] (kz = -J.., ky, kx = -K..), BF16,
+  // row stride feat_ld; feat_gather[b] = offset (c*M + iy) of bin b (or of its
+  // mirror -b) in a pixel's power block.
+  void* feat;
+  int feat_ld;
+  const int* feat_gather;
 };
 
 struct AutocorrArgs {
@@ -64,6 +71,8 @@ struct AutocorrArgs {
   float* vx;
   float* vy;
   float* rs_out;                // optional [H*W][L*L]
+  const int* pix_list;          // optional: evaluate only these pixels ...
+  const int* n_list;            // ... (count on the device)
   const float2* tab_y;          // e^{j2pi ky ly/M}: [L][M]   (index ky+K)
   const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
 };

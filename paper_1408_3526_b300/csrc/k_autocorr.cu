@@ -52,11 +52,11 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     cw[k] = e.x;
     sw[k] = e.y;
   }
-  const long long npix = (long long)a.H * a.W;
+  const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
   for (long long base = ((long long)blockIdx.x * kWarps + wid) * 2; base < npix;
        base += (long long)gridDim.x * kWarps * 2) {
-    const long long pix = base + half;
-    const bool valid = pix < npix;
+    const bool valid = base + half < npix;
+    const long long pix = !valid ? 0 : (a.pix_list ? (long long)a.pix_list[base + half] : base + half);
     // ---- Q sums of this half-warp's pixel ----------------------------------
     if (valid) {
       const float* A = a.Astate + pix * a.kpad;

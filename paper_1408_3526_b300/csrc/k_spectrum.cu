@@ -29,6 +29,8 @@
 //   D  per output pixel, reduce P over kz into A, smooth, store.
 // Register prefetch hides the HBM latency of the next row's frame/observer
 // state (phase A) and of the next output row's smoother state (phase D).
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "common.cuh"
@@ -423,6 +425,24 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
         loadD(yo + 1);
       } else {
         cp_async_commit();
+      }
+      // learned-estimator features of this output row: one warp per pixel
+      if (outrow && a.feat != nullptr) {
+        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+        const int nbins = M * M * MZ;
+        for (int x = wid; x < TW; x += nw) {
+          if (x0 + x >= W) continue;
+          const float* pb = pbuf + x * PS;
+          float tot = 0.f;
+          for (int b = lane; b < nbins; b += 32) tot += pb[a.feat_gather[b]];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+          const float inv = tot > 0.f ? 1.f / tot : 0.f;
+          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.feat) + (size_t(yo) * W + x0 + x) * a.feat_ld;
+          for (int b = lane; b < a.feat_ld; b += 32)
+            dst[b] = __float2bfloat16(
+                b < nbins ? 0.1f * (__log2f(fmaf(pb[a.feat_gather[b]], inv, 1e-6f)) + 10.f) : 0.f);
+        }
       }
       // pbuf, dbuf and the ring slot are rewritten only after the next barriers
     }

@@ -139,6 +139,52 @@ static int pick_tile_w(int M, int Mz) {
   return tw;
 }
 
+// Learned mode: MLP velocity where its confidence passes the threshold (rounded
+// to the grid), the exact autocorrelation search for every other pixel.
+__global__ void learned_select_kernel(const float* y, int npix, float thr, float vmax, float vstep, int L,
+                                      int* vidx, float* vx, float* vy, int* list, int* nlist) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float c = y[3 * p + 2];
+    const float conf = 1.f / (1.f + __expf(-c));
+    if (conf >= thr) {
+      int ix = __float2int_rn((y[3 * p] + vmax) / vstep), iy = __float2int_rn((y[3 * p + 1] + vmax) / vstep);
+      ix = ix < 0 ? 0 : (ix >= L ? L - 1 : ix);
+      iy = iy < 0 ? 0 : (iy >= L ? L - 1 : iy);
+      vidx[p] = iy * L + ix;
+      vx[p] = -vmax + ix * vstep;
+      vy[p] = -vmax + iy * vstep;
+    } else {
+      list[atomicAdd(nlist, 1)] = p;
+    }
+  }
+}
+
+__global__ void accumulate_count_kernel(const int* n, long long* total) { *total += *n; }
+
+extern "C" int wh_mlp_forward(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy);
+
+static int learned_search(wh_stream* s) {
+  const int npix = s->H * s->W;
+  int rc = wh_mlp_forward(s->mlp, s->d_feat, s->feat_ld, npix, s->d_ymlp, 3);
+  if (rc != WH_OK) return rc;
+  WH_CU(cudaMemsetAsync(s->d_nlist, 0, sizeof(int), s->st));
+  learned_select_kernel<<<148 * 8, 256, 0, s->st>>>(s->d_ymlp, npix, s->conf_thr, float(s->vmax),
+                                                    float(s->vstep), s->L, s->vidx, s->vx, s->vy,
+                                                    s->d_list, s->d_nlist);
+  WH_CU(cudaGetLastError());
+  AutocorrArgs aa;
+  aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
+  aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
+  aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
+  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx; aa.pix_list = s->d_list; aa.n_list = s->d_nlist;
+  cudaError_t e = launch_autocorr(aa, s->st);
+  if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel (fallback pixels)");
+  accumulate_count_kernel<<<1, 1, 0, s->st>>>(s->d_nlist, s->d_nfb_total);
+  WH_CU(cudaGetLastError());
+  s->mlp_frames += 1;
+  return WH_OK;
+}
+
 static void fill_tc_args(const wh_stream* s, AutocorrTcArgs& ta) {
   ta.H = s->H; ta.W = s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad; ta.kg = s->kg;
   ta.ntile = s->ntile; ta.mode = s->tc_mode; ta.bf16 = s->tc_bf16;
@@ -153,7 +199,8 @@ static void free_stream(wh_stream* s) {
   void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
                   s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
-                  s->d_table, s->d_err, s->d_nfb};
+                  s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather, s->d_ymlp,
+                  s->d_list, s->d_nlist, s->d_nfb_total};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -208,6 +255,9 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->d_raw = nullptr; s->d_rs = nullptr; s->prof = 0; s->ev_used = 0; s->t = 0; s->cur = 0;
   s->d_a16 = nullptr; s->d_l1 = nullptr; s->d_cval = nullptr; s->d_cidx = nullptr;
   s->d_table = nullptr; s->d_err = nullptr; s->d_nfb = nullptr;
+  s->d_feat = nullptr; s->feat_ld = 0; s->d_fgather = nullptr; s->mlp = nullptr; s->conf_thr = 0.8f;
+  s->d_ymlp = nullptr; s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
+  s->mlp_frames = 0;
   s->tc_mode = pmode == 0 ? 0 : 1;
   s->tc_bf16 = pmode == 2 ? 1 : 0;
   s->use_tc = (pmode != 0) || ((p.precision & WH_PREC_TC_SHORTLIST) && autocorr_tc_supported(M));
@@ -401,11 +451,16 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
+  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
   cudaError_t e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
   if (ev) WH_CU(cudaEventRecord(ev[1], s->st));
   int nlaunch = 3;
-  if (s->use_tc) {
+  if (s->mlp) {
+    const int rc = learned_search(s);
+    if (rc != WH_OK) return rc;
+    nlaunch = 4;
+  } else if (s->use_tc) {
     AutocorrTcArgs ta;
     fill_tc_args(s, ta);
     e = launch_autocorr_convert(ta, s->st);
@@ -424,7 +479,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
     aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
     aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
-    aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
+    aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx; aa.pix_list = nullptr; aa.n_list = nullptr;
     e = launch_autocorr(aa, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
   }
@@ -499,7 +554,7 @@ int wh_read_autocorr(wh_stream* s, float* out, int is_device) {
   aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
   aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
   aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = s->d_rs;
-  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx;
+  aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx; aa.pix_list = nullptr; aa.n_list = nullptr;
   cudaError_t e = launch_autocorr(aa, s->st);
   if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
   g_launches.fetch_add(1);
@@ -523,6 +578,97 @@ int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
     WH_CU(cudaMemcpyAsync(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost, s->st));
     WH_CU(cudaStreamSynchronize(s->st));
   }
+  if (fallback_pixels) *fallback_pixels = h;
+  return WH_OK;
+}
+
+int wh_stream_set_features(wh_stream* s, int enable) {
+  if (!s) return WH_EINVAL;
+  if (!enable) {
+    if (s->mlp) return WH_EINVAL;
+    if (s->d_feat) cudaFree(s->d_feat);
+    if (s->d_fgather) cudaFree(s->d_fgather);
+    s->d_feat = nullptr; s->d_fgather = nullptr; s->feat_ld = 0;
+    return WH_OK;
+  }
+  if (s->d_feat) return WH_OK;
+  const int M = s->M, K = s->K, Mz = s->Mz, J = (Mz - 1) / 2;
+  const bool even = (Mz % 2) == 0;
+  const int npl = J + 1 + (even ? 1 : 0), nb = M * M * Mz;
+  std::vector<int> base(npl);
+  int c = 0;
+  for (int p = 0; p < npl; ++p) {
+    const bool real = (p == 0) || (even && p == npl - 1);
+    base[p] = c;
+    c += real ? K + 1 : M;
+  }
+  auto chan = [&](int p, int kx) {
+    const bool real = (p == 0) || (even && p == npl - 1);
+    return base[p] + (real ? kx : kx + K);
+  };
+  // bin order [kz][ky][kx]: the bin itself if its plane/channel is stored, else its mirror
+  std::vector<int> fg(nb);
+  for (int iz = 0; iz < Mz; ++iz)
+    for (int iy = 0; iy < M; ++iy)
+      for (int ix = 0; ix < M; ++ix) {
+        int kz = iz - J, ky = iy - K, kx = ix - K;
+        const bool nyq = even && kz == Mz / 2;
+        bool stored = kz >= 0 && kz <= (even ? Mz / 2 : J);
+        const bool real = kz == 0 || nyq;
+        if (stored && real && kx < 0) stored = false;
+        if (!stored) {
+          kx = -kx; ky = -ky;
+          if (!nyq) kz = -kz;
+        }
+        fg[(iz * M + iy) * M + ix] = chan(kz, kx) * M + (ky + K);
+      }
+  s->feat_ld = (nb + 7) / 8 * 8;
+  cudaError_t e = cudaMalloc(&s->d_feat, 2 * size_t(s->H) * s->W * s->feat_ld);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_fgather, sizeof(int) * nb);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_fgather, fg.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->d_feat, 0, 2 * size_t(s->H) * s->W * s->feat_ld);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? WH_ENOMEM : set_cuda_err(e, "features");
+  return WH_OK;
+}
+
+int wh_read_features(wh_stream* s, void* out, int is_device, int* ld) {
+  if (!s || !s->d_feat) return WH_EINVAL;
+  if (ld) *ld = s->feat_ld;
+  if (!out) return WH_OK;
+  return copy_out(s, out, s->d_feat, 2 * size_t(s->H) * s->W * s->feat_ld, is_device);
+}
+
+int wh_stream_set_learned(wh_stream* s, wh_mlp* mlp, float conf_threshold) {
+  if (!s) return WH_EINVAL;
+  if (!mlp) {
+    s->mlp = nullptr;
+    return WH_OK;
+  }
+  int rc = wh_stream_set_features(s, 1);
+  if (rc != WH_OK) return rc;
+  const size_t npix = size_t(s->H) * s->W;
+  cudaError_t e = cudaSuccess;
+  if (!s->d_ymlp) e = cudaMalloc((void**)&s->d_ymlp, sizeof(float) * 3 * npix);
+  if (e == cudaSuccess && !s->d_list) e = cudaMalloc((void**)&s->d_list, sizeof(int) * npix);
+  if (e == cudaSuccess && !s->d_nlist) e = cudaMalloc((void**)&s->d_nlist, sizeof(int));
+  if (e == cudaSuccess && !s->d_nfb_total) {
+    e = cudaMalloc((void**)&s->d_nfb_total, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(s->d_nfb_total, 0, sizeof(long long));
+  }
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? WH_ENOMEM : set_cuda_err(e, "learned mode");
+  s->mlp = mlp;
+  s->conf_thr = conf_threshold;
+  return WH_OK;
+}
+
+int wh_stream_learned_stats(wh_stream* s, long long* frames, long long* fallback_pixels) {
+  if (!s) return WH_EINVAL;
+  long long h = 0;
+  if (s->d_nfb_total) {
+    WH_CU(cudaMemcpyAsync(&h, s->d_nfb_total, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+    WH_CU(cudaStreamSynchronize(s->st));
+  }
+  if (frames) *frames = s->mlp_frames;
   if (fallback_pixels) *fallback_pixels = h;
   return WH_OK;
 }

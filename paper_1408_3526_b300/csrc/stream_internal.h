@@ -40,6 +40,17 @@ struct wh_stream {
   void* d_table;
   int* d_err;
   int* d_nfb;
+  // learned-estimator features and learned velocity mode
+  void* d_feat;          // BF16 [H*W][feat_ld]
+  int feat_ld;
+  int* d_fgather;        // [M*M*Mz]
+  struct wh_mlp* mlp;    // not owned
+  float conf_thr;
+  float* d_ymlp;         // [H*W][3]
+  int* d_list;           // [H*W] pixels sent to the exact search
+  int* d_nlist;          // [1]
+  long long* d_nfb_total;// fallback pixels accumulated
+  long long mlp_frames;
   // per-kernel timing (wh_profile_enable)
   int prof;
   std::vector<cudaEvent_t> ev;   // 4 per timed frame

@@ -226,6 +226,25 @@ def sinusoid_scene(H, W, T, comps, vx, vy, dc=0.0):
     return frames
 
 
+def training_scene_set(n_scenes, T, H, W, seed0=100, vlim=1.75, tex_size=2048, noise_rel=0.02):
+    """Yield (frames [T][H][W], (vx, vy)) for n_scenes config-1-style scenes:
+    one 1/f^2 texture (seed seed0), each scene a random window origin and a
+    uniform velocity drawn U[-vlim, vlim]^2 (scene seed = seed0 + i), additive
+    white noise of noise_rel x RMS."""
+    tex = make_texture(tex_size, seed0)
+    for i in range(n_scenes):
+        rng = np.random.default_rng(seed0 + i)
+        vx, vy = rng.uniform(-vlim, vlim, 2)
+        ox, oy = rng.uniform(0, tex_size, 2)
+        back0, _ = uniform_flow(vx, vy)
+
+        def back(px, py, t, ox=ox, oy=oy, back0=back0):
+            sx, sy = back0(px, py, t)
+            return sx + ox, sy + oy
+        frames = _render(tex, H, W, T, back, [], noise_rel, 10.0, seed0 + i)
+        yield frames, (float(vx), float(vy))
+
+
 def paper_sim_scene(T=32, H=64, W=64, seed=5):
     """The paper's own simulation recipe (Sec. 3), re-generated from its text.
 
