@@ -275,6 +275,41 @@ int wh_stream_set_learned(wh_stream *s, wh_mlp *mlp, float conf_threshold);
 /* Frames processed in learned mode and pixel-frames sent to the search. */
 int wh_stream_learned_stats(wh_stream *s, long long *frames, long long *fallback_pixels);
 
+/* ---- multi-stream serving --------------------------------------------------
+ * Many sensor streams of different sizes and parameters share one GPU; each
+ * stream's recursive state stays resident on the device.  The paper processes
+ * one stream; this runtime is an addition of the library.
+ *   open    admits a stream if its device footprint (wh_stream_device_bytes)
+ *           fits in what is left of the budget, else WH_EADMIT.
+ *   submit  queues one frame (host memory, copied into a pinned slot) with its
+ *           arrival time on the server clock (wh_server_now); a stream with
+ *           queue_limit frames already waiting rejects it with WH_EADMIT
+ *           (back-pressure; counted as shed).
+ *   A dispatcher thread keeps up to max_inflight frames on the GPU, oldest
+ *   arrival first among streams whose previous frame has left the queue; each
+ *   stream runs on one of n_cuda_streams CUDA streams, so different streams'
+ *   frames overlap on the device while one stream's frames stay in order.
+ *   wait    blocks until a request completes; returns its whitened frame
+ *           (if keep_results) and its latency = completion - arrival.
+ *   stats   p50/p99 latency of served frames, served Mpixel/s between the
+ *           first arrival and the last completion, served/shed/submitted.
+ */
+typedef struct wh_server wh_server;
+long long wh_stream_device_bytes(int h, int w, int window, int temporal_order, wh_vgrid grid);
+int wh_server_create(double hbm_budget_bytes, int max_inflight, int queue_limit, int n_cuda_streams,
+                     int keep_results, wh_server **out);
+int wh_server_open(wh_server *srv, int h, int w, int window, int temporal_order, wh_vgrid grid,
+                   const wh_params *opt, int *stream_id);
+int wh_server_submit(wh_server *srv, int stream_id, const float *frame, double arrival_s,
+                     long long *request_id);
+double wh_server_now(wh_server *srv);
+int wh_server_wait(wh_server *srv, long long request_id, float *whitened, double *latency_s);
+int wh_server_drain(wh_server *srv);
+int wh_server_stats(wh_server *srv, double *p50_ms, double *p99_ms, double *mpix_per_s,
+                    long long *served, long long *shed, long long *submitted);
+int wh_server_close(wh_server *srv, int stream_id);
+int wh_server_destroy(wh_server *srv);
+
 /* Reset the recursive state to zero (as if no frame had been pushed). */
 int wh_reset_stream(wh_stream *s);
 

@@ -89,6 +89,18 @@ _SIGS = {
     "wh_read_features": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(C.c_int)]),
     "wh_stream_set_learned": (C.c_int, [_VP, _VP, C.c_float]),
     "wh_stream_learned_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "wh_stream_device_bytes": (C.c_longlong, [C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid]),
+    "wh_server_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
+    "wh_server_open": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid, C.POINTER(wh_params),
+                                 C.POINTER(C.c_int)]),
+    "wh_server_submit": (C.c_int, [_VP, C.c_int, _VP, C.c_double, C.POINTER(C.c_longlong)]),
+    "wh_server_now": (C.c_double, [_VP]),
+    "wh_server_wait": (C.c_int, [_VP, C.c_longlong, _VP, C.POINTER(C.c_double)]),
+    "wh_server_drain": (C.c_int, [_VP]),
+    "wh_server_stats": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "wh_server_close": (C.c_int, [_VP, C.c_int]),
+    "wh_server_destroy": (C.c_int, [_VP]),
     "wh_reset_stream": (C.c_int, [_VP]),
     "wh_destroy_stream": (C.c_int, [_VP]),
     "wh_status_string": (C.c_char_p, [C.c_int]),

@@ -81,3 +81,11 @@ def test_product_never_imports_the_oracle():
             txt = open(path).read()
             assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), path
             assert "whiten_oracle" not in txt, path
+
+
+def test_stream_device_bytes_estimate(lib):
+    g = _abi.wh_vgrid(3.0, 0.25)
+    a = lib.wh_stream_device_bytes(512, 640, 15, 6, g)
+    b = lib.wh_stream_device_bytes(1024, 1280, 15, 6, g)
+    assert a > 512 * 640 * (4 * 228) and 3.9 < b / a < 4.1
+    assert lib.wh_stream_device_bytes(0, 640, 15, 6, g) == -1
