@@ -41,7 +41,7 @@ namespace {
 
 constexpr int kPrefA = kMaxMz + 1;   // frame + Mz state floats per phase-A pixel
 constexpr int kMaxDTasks = 4;        // phase-D tasks per thread (checked on the host)
-constexpr int kSpecMaxThreads = 384;
+constexpr int kSpecMaxThreads = 384;   // y-SDFT threads rounded to warps + one observer warp
 constexpr int kMaxBTasks = 2;        // phase-B tasks per thread (checked on the host)
 
 template <int M, int MZ>
@@ -72,7 +72,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __host__ __device__ inline int spec_threads_for(int M, int Mz, int tw) {
   const int K = (M - 1) / 2, J = (Mz - 1) / 2;
   const int nchy = (1 + ((Mz % 2) == 0 ? 1 : 0)) * (K + 1) + J * M;
-  return ((tw * nchy + 31) / 32) * 32;
+  return ((tw * nchy + 31) / 32) * 32 + 32;      // + the observer warp
 }
 
 // Byte offsets of the shared-memory arrays (16-byte aligned each); the same
@@ -239,42 +239,45 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     float2 drun[kMaxBTasks];
 #pragma unroll
     for (int q = 0; q < kMaxBTasks; ++q) drun[q] = make_float2(0.f, 0.f);
+    const int nrows = TH + 2 * K;
 
-    // phase-A prefetch of input row i into this thread's slot of abuf
-    auto loadA = [&](int i) {
-      if (tid < RW) {
-        const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + tid, W);
+    // The last warp runs the observer update of the next input row while the
+    // other warps run the y-recursion of the current one.
+    const int ua = tid - (nthr - 32);
+    const bool athr = ua >= 0 && ua < RW;
+    float pa[kPrefA];
+    auto loadA = [&](int i) {             // prefetch input row i into this lane's abuf slot
+      if (athr) {
+        const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + ua, W);
         const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
-        float* dst = abuf + tid * kPrefA;
+        float* dst = abuf + ua * kPrefA;
         cp_async4(dst, a.frame + o);
 #pragma unroll
         for (int f = 0; f < MZ; ++f) cp_async4(dst + 1 + f, a.obs_old + f * plane + o);
       }
       cp_async_commit();
     };
-    loadA(0);
-    float pa[kPrefA];
-    auto readA = [&]() {
-      cp_async_wait1();
-      if (tid < RW) {
+    auto doA = [&](int i) {               // observer update + Hann(kz) of input row i
+      if (!athr) return;
+      const int r = y0 - K + i;
 #pragma unroll
-        for (int f = 0; f <= MZ; ++f) pa[f] = abuf[tid * kPrefA + f];
+      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[ua * kPrefA + f];
+      float2 T[NPL], Tw[NPL];
+      observer_hann<M, MZ>(pa, lam, hz, T, Tw);
+      const int xs = x0 - K + ua;
+      if (r >= y0 && r < y1 && ua >= K && ua < K + TW && xs < W) {   // owner writes the new state
+        const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
+        a.obs_new[o] = T[0].x;
+#pragma unroll
+        for (int j = 1; j <= J; ++j) {
+          a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
+          a.obs_new[(2 * j) * plane + o] = T[j].y;
+        }
+        if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
       }
-    };
-    // Per-plane offset removed from every Tw of this segment before the spatial
-    // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
-    // spatially constant offset per temporal plane (it only feeds the removed
-    // kx = ky = 0 bin and the correction that cancels its window leakage), so
-    // subtracting one constant per segment leaves the result unchanged while
-    // keeping the FP32 sums at the scale of the texture instead of the DC level.
-    if (tid == 0) {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[f];
-      float2 Tn[NPL], Tw0[NPL];
-      observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
-    }
+      for (int p = 0; p < NPL; ++p) twr[p * RW + ua] = csub(Tw[p], offs[p]);
+    };
     // phase-D prefetch of the smoother state of an output row (own slots of dpre)
     auto loadD = [&](int yo) {
 #pragma unroll
@@ -288,38 +291,9 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
       }
       cp_async_commit();
     };
-    loadD(y0);
-    __syncthreads();
-
-    const int nrows = TH + 2 * K;
-    for (int i = 0; i < nrows; ++i) {
-      const int r = y0 - K + i;               // input row (unclamped)
-      // ---------------- A: observer update + Hann along kz -------------------
-      readA();
-      if (tid < RW) {
-        float2 T[NPL], Tw[NPL];
-        observer_hann<M, MZ>(pa, lam, hz, T, Tw);
-        const int xs = x0 - K + tid;
-        if (r >= y0 && r < y1 && tid >= K && tid < K + TW && xs < W) {   // owner writes
-          const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
-          a.obs_new[o] = T[0].x;
-#pragma unroll
-          for (int j = 1; j <= J; ++j) {
-            a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
-            a.obs_new[(2 * j) * plane + o] = T[j].y;
-          }
-          if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
-        }
-#pragma unroll
-        for (int p = 0; p < NPL; ++p) twr[p * RW + tid] = csub(Tw[p], offs[p]);
-      }
-      if (i + 1 < nrows) loadA(i + 1);
-      else cp_async_commit();
-      __syncthreads();
-
-      // ---------------- B: x-DFT of the row into the ring -------------------
+    auto doB = [&](int i) {               // x-DFT of input row i into ring slot i mod (M+1)
       const int slot = i % (M + 1);
-      const int oslot = (i + 1) % (M + 1);    // == (i - M) mod (M + 1)
+      const int oslot = (i + 1) % (M + 1);    // holds row i - M
 #pragma unroll
       for (int q = 0; q < kMaxBTasks; ++q) {
         const int bt = btask[q];
@@ -351,83 +325,78 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
         }
         ring[(slot * nch + c) * TW + x] = acc;
       }
-      __syncthreads();
-
-      // ---------------- C: y-SDFT, Hann(ky), high-pass, power ----------------
-      const int yo = r - K;                    // output row of this window
-      const bool outrow = (i >= 2 * K) && (yo < y1);
-      if (yth) {
-        const float2 xn = ring[(slot * nch + cy) * TW + xy];
-        float2 d = xn;
-        if (i >= M) d = csub(xn, ring[(oslot * nch + cy) * TW + xy]);
+    };
+    auto doC = [&](int i) {               // y-SDFT, Hann(ky), high-pass, power of row i
+      if (!yth) return;
+      const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);
+      const int yo = y0 + i - 2 * K;
+      const float2 xn = ring[(slot * nch + cy) * TW + xy];
+      float2 d = xn;
+      if (i >= M) d = csub(xn, ring[(oslot * nch + cy) * TW + xy]);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          const float2 w = c_wres[MI][k], c = c_cph[MI][k];
-          Y[k] = make_float2(fmaf(w.x, Y[k].x, fmaf(-w.y, Y[k].y, fmaf(c.x, d.x, -c.y * d.y))),
-                             fmaf(w.x, Y[k].y, fmaf(w.y, Y[k].x, fmaf(c.x, d.y, c.y * d.x))));
-        }
-        if (outrow) {
-          // Hann along ky (real taps 1/4, 1/2, 1/4 in the centred basis), minus
-          // Hann_x Hann_y of the removed (0,0) bin, then the power.
-          float2 D = make_float2(0.f, 0.f);
-          float wxh = 0.f;
-          if (kxc >= -1 && kxc <= 1) {
-            D = dbuf[plc * TW + xy];
-            wxh = (kxc == 0) ? 0.5f : 0.25f;
-          }
-          float* pb = pbuf + xy * PS + cy * M;
-          const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
+      for (int k = 0; k < M; ++k) {
+        const float2 w = c_wres[MI][k], c = c_cph[MI][k];
+        Y[k] = make_float2(fmaf(w.x, Y[k].x, fmaf(-w.y, Y[k].y, fmaf(c.x, d.x, -c.y * d.y))),
+                           fmaf(w.x, Y[k].y, fmaf(w.y, Y[k].x, fmaf(c.x, d.y, c.y * d.x))));
+      }
+      if (!(i >= 2 * K && yo < y1)) return;
+      // 4 x [Hann along ky (taps 1/4, 1/2, 1/4 in the centred basis), minus
+      // Hann_x Hann_y of the removed (0,0) bin]; the factor 16 is in the power scale
+      float2 D = make_float2(0.f, 0.f);
+      float wxh = 0.f;
+      if (kxc >= -1 && kxc <= 1) {
+        D = dbuf[plc * TW + xy];
+        wxh = (kxc == 0) ? 0.5f : 0.25f;
+      }
+      float* pb = pbuf + xy * PS + cy * M;
+      const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
+      const float sP16 = sP * (1.f / 16.f);
 #pragma unroll
-          for (int k = 0; k < M; ++k) {
-            float2 z = cadd(cscale(Y[k], 0.5f), cscale(cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]), 0.25f));
-            if (k == K) z = csub(z, cscale(D, wxh * 0.5f));
-            if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh * 0.25f));
-            const float pw = sP * fmaf(z.x, z.x, z.y * z.y);
-            pb[k] = pw;
-            if (dump) {
-              // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
-              const size_t pix = size_t(yo) * W + x0 + xy;
-              const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
-              const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
-                                       float(MZ) / sqrtf(float(M * M * MZ)));
-              const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
-              const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
-              a.dump_win[op] = sv;
-              a.dump_win[om] = conjf2(sv);
-              if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
-            }
-          }
+      for (int k = 0; k < M; ++k) {
+        float2 z = cadd(cscale(Y[k], 2.f), cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]));
+        if (k == K) z = csub(z, cscale(D, wxh * 2.f));
+        if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh));
+        const float pw = sP16 * fmaf(z.x, z.x, z.y * z.y);
+        pb[k] = pw;
+        if (dump) {
+          // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
+          const size_t pix = size_t(yo) * W + x0 + xy;
+          const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
+          const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
+                                   0.25f * float(MZ) / sqrtf(float(M * M * MZ)));
+          const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
+          const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
+          a.dump_win[op] = sv;
+          a.dump_win[om] = conjf2(sv);
+          if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
         }
       }
-      __syncthreads();
-
-      // ---------------- D: reduce over kz, smooth, store ---------------------
-      cp_async_wait1();
-      if (outrow) {
+    };
+    auto doD = [&](int i) {               // reduce over kz, smooth, store (output row of i)
+      const int yo = y0 + i - 2 * K;
+      if (!(i >= 2 * K && yo < y1)) return;
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < kMaxDTasks; ++q) {
-          const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
-          if (dtask[q] < 0 || x0 + x >= W) continue;
-          const int* g = hg + hi * nslot;
-          const float* pb = pbuf + x * PS;
-          float Ac = pb[g[0]], As = 0.f;
+      for (int q = 0; q < kMaxDTasks; ++q) {
+        const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
+        if (dtask[q] < 0 || x0 + x >= W) continue;
+        const int* g = hg + hi * nslot;
+        const float* pb = pbuf + x * PS;
+        float Ac = pb[g[0]], As = 0.f;
 #pragma unroll
-          for (int j = 1; j <= J; ++j) {
-            const float pp = pb[g[j]], pm = pb[g[J + j]];
-            Ac = fmaf(pp + pm, tb.cz[j], Ac);
-            As = fmaf(pp - pm, tb.sz[j], As);
-          }
-          if (EVEN) Ac -= pb[g[2 * J + 1]];
-          float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-          dst[hi] = fmaf(oma, Ac, alpha * dpre[(q * 2 + 0) * nthr + tid]);
-          if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * dpre[(q * 2 + 1) * nthr + tid]);
+        for (int j = 1; j <= J; ++j) {
+          const float pp = pb[g[j]], pm = pb[g[J + j]];
+          Ac = fmaf(pp + pm, tb.cz[j], Ac);
+          As = fmaf(pp - pm, tb.sz[j], As);
         }
-        loadD(yo + 1);
-      } else {
-        cp_async_commit();
+        if (EVEN) Ac -= pb[g[2 * J + 1]];
+        float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
+        dst[hi] = fmaf(oma, Ac, alpha * dpre[(q * 2 + 0) * nthr + tid]);
+        if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * dpre[(q * 2 + 1) * nthr + tid]);
       }
+      loadD(yo + 1);
       // learned-estimator features of this output row: one warp per pixel
-      if (outrow && a.feat != nullptr) {
+      if (a.feat != nullptr) {
         const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
         const int nbins = M * M * MZ;
         for (int x = wid; x < TW; x += nw) {
@@ -444,7 +413,45 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
                 b < nbins ? 0.1f * (__log2f(fmaf(pb[a.feat_gather[b]], inv, 1e-6f)) + 10.f) : 0.f);
         }
       }
-      // pbuf, dbuf and the ring slot are rewritten only after the next barriers
+    };
+
+    // ---- prologue: offsets, observer of row 0, x-DFT of row 0 ----------------
+    loadA(0);
+    // Per-plane offset removed from every Tw of this segment before the spatial
+    // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
+    // spatially constant offset per temporal plane (it only feeds the removed
+    // kx = ky = 0 bin and the correction that cancels its window leakage), so
+    // subtracting one constant per segment leaves the result unchanged while
+    // keeping the FP32 sums at the scale of the texture instead of the DC level.
+    if (ua == 0) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[f];
+      float2 Tn[NPL], Tw0[NPL];
+      observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
+    }
+    loadD(y0);
+    __syncthreads();
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    doA(0);
+    if (nrows > 1) loadA(1);
+    __syncthreads();
+    doB(0);
+    __syncthreads();
+
+    // ---- pipelined rows: X = {y-SDFT(i), observer(i+1)}, Y = {reduce(i), x-DFT(i+1)}
+    for (int i = 0; i < nrows; ++i) {
+      doC(i);
+      if (i + 1 < nrows) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        doA(i + 1);
+        if (i + 2 < nrows) loadA(i + 2);
+      }
+      __syncthreads();
+      doD(i);
+      if (i + 1 < nrows) doB(i + 1);
+      __syncthreads();
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();   // before the next segment rewrites offs
@@ -457,11 +464,7 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
 struct SpecLaunch { int threads; size_t smem; };
 
 static SpecLaunch spec_launch_shape(int M, int Mz, int tw) {
-  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
-  const bool even = (Mz % 2) == 0;
-  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
-  int threads = ((tw * nchy + 31) / 32) * 32;
-  return {threads, spec_smem_layout(M, Mz, tw).total};
+  return {spec_threads_for(M, Mz, tw), spec_smem_layout(M, Mz, tw).total};
 }
 
 template <int M, int MZ>

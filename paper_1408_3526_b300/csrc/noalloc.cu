@@ -119,12 +119,13 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
     src = s->frame;
   }
   // 1. spectrum, observer and smoothing (same kernel as wh_push_frame)
-  SpecArgs sa;
+  SpecArgs sa{};
   sa.H = s->H; sa.W = s->W; sa.M = s->M; sa.Mz = s->Mz; sa.tw = s->tw; sa.th = s->th;
   sa.kpad = s->kpad; sa.alpha = float(s->alpha); sa.frame = src;
   sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
+  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
   e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return wh_cuda_fail(e, "spectrum kernel");
   // 2. autocorrelation search with all scratch in the static array
@@ -135,7 +136,7 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
   long long launches = 2;
   for (size_t p0 = 0; p0 < npix; p0 += kChunk) {
     const int n = int(npix - p0 < size_t(kChunk) ? npix - p0 : size_t(kChunk));
-    AutocorrTcArgs ta;
+    AutocorrTcArgs ta{};
     ta.H = 1; ta.W = n; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad; ta.kg = kKg;
     ta.ntile = (s->L * s->L + 127) / 128; ta.mode = 0; ta.bf16 = 0;
     ta.vmax = float(s->vmax); ta.vstep = float(s->vstep);
@@ -153,7 +154,7 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
     launches += 3;
   }
   // 3. prediction-error filter (same kernel as wh_push_frame)
-  PefArgs pa;
+  PefArgs pa{};
   pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
   pa.obs = s->obs[1 - s->cur]; pa.vidx = s->vidx; pa.hw = s->d_hw; pa.whitened = s->whitened;
   e = launch_pef(pa, s->st);

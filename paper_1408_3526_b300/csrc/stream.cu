@@ -133,9 +133,10 @@ static int pick_tile_w(int M, int Mz) {
   const int K = (M - 1) / 2, J = (Mz - 1) / 2;
   const bool even = (Mz % 2) == 0;
   const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
-  int tw = 384 / nchy;         // <= 384 threads: two CTAs per SM
-  if (tw > 32) tw = 32;
-  if (tw < 1) tw = 1;
+  // y-SDFT threads (rounded to warps) + one observer warp <= 384: two CTAs per SM
+  // and the row segment tw + 2K is covered by the observer warp's 32 lanes
+  int tw = 32 - 2 * K;
+  while (tw > 1 && ((tw * nchy + 31) / 32) * 32 + 32 > 384) --tw;
   return tw;
 }
 
@@ -172,7 +173,7 @@ static int learned_search(wh_stream* s) {
                                                     float(s->vstep), s->L, s->vidx, s->vx, s->vy,
                                                     s->d_list, s->d_nlist);
   WH_CU(cudaGetLastError());
-  AutocorrArgs aa;
+  AutocorrArgs aa{};
   aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
   aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
   aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
@@ -445,7 +446,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     s->ev_used += 4;
   }
   if (ev) WH_CU(cudaEventRecord(ev[0], s->st));
-  SpecArgs sa;
+  SpecArgs sa{};
   sa.H = s->H; sa.W = s->W; sa.M = s->M; sa.Mz = s->Mz; sa.tw = s->tw; sa.th = s->th;
   sa.kpad = s->kpad; sa.alpha = float(s->alpha); sa.frame = src;
   sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
@@ -461,7 +462,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     if (rc != WH_OK) return rc;
     nlaunch = 4;
   } else if (s->use_tc) {
-    AutocorrTcArgs ta;
+    AutocorrTcArgs ta{};
     fill_tc_args(s, ta);
     e = launch_autocorr_convert(ta, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation convert kernel");
@@ -475,7 +476,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation re-rank kernel");
     nlaunch = 5;
   } else {
-    AutocorrArgs aa;
+    AutocorrArgs aa{};
     aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
     aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
     aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
@@ -484,7 +485,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
   }
   if (ev) WH_CU(cudaEventRecord(ev[2], s->st));
-  PefArgs pa;
+  PefArgs pa{};
   pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
   pa.obs = s->obs[1 - s->cur]; pa.vidx = s->vidx; pa.hw = s->d_hw; pa.whitened = s->whitened;
   e = launch_pef(pa, s->st);
@@ -532,7 +533,7 @@ int wh_read_spectrum(wh_stream* s, int kind, void* out, int is_device) {
   const size_t nb = size_t(s->H) * s->W * s->M * s->M * s->Mz;
   if (kind == WH_SPEC_RAW) {
     if (!s->d_raw) WH_CU(cudaMalloc((void**)&s->d_raw, sizeof(float2) * nb));
-    RawSpecArgs ra;
+    RawSpecArgs ra{};
     ra.H = s->H; ra.W = s->W; ra.M = s->M; ra.Mz = s->Mz; ra.obs = s->obs[s->cur]; ra.out = s->d_raw;
     cudaError_t e = launch_raw_spectrum(ra, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "raw spectrum kernel");
@@ -550,7 +551,7 @@ int wh_read_autocorr(wh_stream* s, float* out, int is_device) {
   if (s->t < 1) return WH_ENOTREADY;
   const size_t n = size_t(s->H) * s->W * s->L * s->L;
   if (!s->d_rs) WH_CU(cudaMalloc((void**)&s->d_rs, sizeof(float) * n));
-  AutocorrArgs aa;
+  AutocorrArgs aa{};
   aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
   aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
   aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = s->d_rs;
