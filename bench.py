@@ -185,6 +185,9 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--precision", type=int, default=0,
+                    help="wh_params.precision (0: FP32-exact search on CUDA cores; 16: tensor-core "
+                         "shortlist + exact re-rank)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -205,7 +208,7 @@ def main():
     frames_h = make_frames(seed=2 + rank)
     frames_d = torch.from_numpy(frames_h).cuda()
     stream = torch.cuda.Stream()
-    s = WhitenStream(H, W, M, MZ, VMAX, VSTEP, cuda_stream=stream)
+    s = WhitenStream(H, W, M, MZ, VMAX, VSTEP, cuda_stream=stream, precision=args.precision)
     # warm-up (state evolves; the work per frame is data-independent)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -279,7 +282,8 @@ def main():
             "config": {"workload": WORKLOAD, "frames_resident": NFRAMES_RESIDENT,
                        "l2": "inputs larger than L2 (smoothed state 295 MB per stream)",
                        "parallelism": f"{world} independent streams" if world > 1 else "1 stream",
-                       "bytes_per_px_algorithmic": BYTES_PER_PX},
+                       "bytes_per_px_algorithmic": BYTES_PER_PX,
+                       "engine": "FP32-exact search on CUDA cores"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved_dom, 1),
                          "peak": hbm, "unit": "GB/s", "frac": round(achieved_dom / hbm, 4),
                          "traffic": None, "peak_source": src,
@@ -291,6 +295,12 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if args.precision:
+            import ctypes as C
+            fb = C.c_longlong()
+            s.lib.wh_stream_stats(s._s, C.byref(fb))
+            line["config"]["engine"] = "tensor-core shortlist + exact re-rank"
+            line["config"]["full_grid_fallback_pixel_frames"] = int(fb.value)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(frames_h)
         print(json.dumps(line), flush=True)

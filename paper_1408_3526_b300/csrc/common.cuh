@@ -81,13 +81,15 @@ struct AutocorrTcArgs {
   int H, W, M, L, kpad;
   int kg;                       // leading dimension of a16 and the table (M^2 rounded up to 8)
   int ntile;                    // 128-column tiles of the grid
+  int ncand;                    // shortlist entries per pixel (cand_* row stride)
+  int ovf_group;                // entries per shortlist group (last of a group inside the window -> incomplete)
   int mode;                     // 0: exact FP32 re-rank of the shortlist; 1: tensor-core value decides
   int bf16;
   float vmax, vstep;
   const float* Astate;
   void* a16;                    // [H*W][kg] F16 or BF16
   float* l1;                    // [H*W] sum |a16|
-  float* cand_val;              // [H*W][ntile][4]
+  float* cand_val;              // [H*W][ncand]
   int* cand_idx;
   int* vidx;
   float* vx;

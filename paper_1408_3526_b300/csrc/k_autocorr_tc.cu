@@ -7,16 +7,17 @@
 //   1. ac_convert: per pixel, scale a by a power of two so max|a| < 1 (the
 //      argmax is scale-invariant and the scaling is exact) and round to F16
 //      (or BF16); also keep sum|a~| for the error bound.
-//   2. tcgen05 GEMM [pixels x 232] x [232 x 640] with a top-4-per-128-column
-//      epilogue: a shortlist of the largest R~(l) of every pixel.
+//   2. tcgen05 contraction [pixels x 232] x [232 x 640] (persistent, the
+//      pixel block resident while the grid table streams; tc_rgemm.cu) whose
+//      epilogue keeps each pixel's 8 largest R~(l) over the whole grid.
 //   3. ac_rerank (FP32-exact mode): every shortlisted l with R~(l) >= max R~ -
 //      2E is re-evaluated exactly in FP32 on CUDA cores (separable form, as in
 //      the CUDA-core search) and the largest wins (ties -> lowest index).  E
 //      bounds |R~ - R| from the operand rounding (2^-11 relative per F16
 //      operand, 2^-25 absolute below the normal range, |B| <= 2) and F32
-//      accumulation of 225 terms.  If some tile's 4th candidate is inside the
-//      window the shortlist may be incomplete and the whole grid is evaluated
-//      exactly for that pixel.  The result equals the exact FP32 argmax.
+//      accumulation of 225 terms.  If the last entry of a shortlist group is
+//      inside the window the shortlist may be incomplete and the whole grid is
+//      evaluated exactly for that pixel.  The result equals the exact FP32 argmax.
 //      Precision-study modes (F16 / BF16 alone) take the GEMM's best directly.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -85,19 +86,21 @@ __device__ __forceinline__ float exact_R(const float* qbuf, const float2* tabx, 
   const float2* tx = tabx + (gc + (jx < 0 ? -jx : jx)) * (K + 1);
   const float4* q4 = reinterpret_cast<const float4*>(qbuf);
   const float2* q0 = reinterpret_cast<const float2*>(qbuf + 4 * (K + 1) * K);
-  float t0r = 0.f, v1 = 0.f, v2 = 0.f;
+  float ry[K], iy[K];                 // cos/sin(2pi ky |ly|/M), ky = 1..K
 #pragma unroll
+  for (int ky = 0; ky < K; ++ky) { const float2 w = ty[ky + 1]; ry[ky] = w.x; iy[ky] = w.y; }
+  float t0r = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll 1
   for (int kx = 0; kx <= K; ++kx) {
     const float2 z = q0[kx];
     float va = z.x, vb = 0.f, vc = 0.f, vd = z.y;
 #pragma unroll
     for (int ky = 0; ky < K; ++ky) {
       const float4 q = q4[kx * K + ky];
-      const float2 w = ty[ky + 1];
-      va = fmaf(q.x, w.x, va);
-      vb = fmaf(q.w, w.y, vb);
-      vc = fmaf(q.y, w.y, vc);
-      vd = fmaf(q.z, w.x, vd);
+      va = fmaf(q.x, ry[ky], va);
+      vb = fmaf(q.w, iy[ky], vb);
+      vc = fmaf(q.y, iy[ky], vc);
+      vd = fmaf(q.z, ry[ky], vd);
     }
     const float tr = jy >= 0 ? va - vb : va + vb;
     const float ti = jy >= 0 ? vc + vd : vd - vc;
@@ -112,10 +115,10 @@ __device__ __forceinline__ float exact_R(const float* qbuf, const float2* tabx, 
 }
 
 template <int M>
-__global__ void __launch_bounds__(kWarpsR * 32) ac_rerank_kernel(const AutocorrTcArgs a) {
+__global__ void __launch_bounds__(kWarpsR * 32, 4) ac_rerank_kernel(const AutocorrTcArgs a) {
   constexpr int K = (M - 1) / 2;
   constexpr int QN = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;
-  const int L = a.L, nh = (M * M - 1) / 2, nt = a.ntile, ncand = nt * 4;
+  const int L = a.L, nh = (M * M - 1) / 2, ncand = a.ncand, og = a.ovf_group;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tabx = reinterpret_cast<float2*>(smem_raw);                            // [L][K+1]
@@ -143,10 +146,12 @@ __global__ void __launch_bounds__(kWarpsR * 32) ac_rerank_kernel(const AutocorrT
       for (int off = 16; off > 0; off >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, off));
       best_i = bi;
     } else {
-      const float E = 4.1e-3f * a.l1[pix] + 3e-5f;
+      // |R~ - R| <= sum_k (|da_k||B| + |a_k||dB|) + accumulation <= 2^-9 sum|a~| (F16
+      // operands, |B| <= 2) + 225 * 2^-23 * 2 sum|a~| + subnormal flush of a~ (2^-25 each)
+      const float E = 2.05e-3f * a.l1[pix] + 2e-5f;
       const float thr = vmax - 2.f * E;
-      // a tile whose 4th best is inside the window may hide further candidates
-      const bool ovf_lane = (lane < ncand) && ((lane & 3) == 3) && (cv >= thr);
+      // a group whose last entry is inside the window may hide further candidates
+      const bool ovf_lane = (lane < ncand) && ((lane % og) == og - 1) && (cv >= thr);
       const bool overflow = __any_sync(0xffffffffu, ovf_lane);
       // Q sums of the pixel (exact FP32 state)
       const float* A = a.Astate + pix * a.kpad;

@@ -138,7 +138,7 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
     const int n = int(npix - p0 < size_t(kChunk) ? npix - p0 : size_t(kChunk));
     AutocorrTcArgs ta{};
     ta.H = 1; ta.W = n; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad; ta.kg = kKg;
-    ta.ntile = (s->L * s->L + 127) / 128; ta.mode = 0; ta.bf16 = 0;
+    ta.ntile = (s->L * s->L + 127) / 128; ta.ncand = ta.ntile * 4; ta.ovf_group = 4; ta.mode = 0; ta.bf16 = 0;
     ta.vmax = float(s->vmax); ta.vstep = float(s->vstep);
     ta.Astate = s->Astate + p0 * s->kpad;
     ta.a16 = sc->a16; ta.l1 = sc->l1; ta.cand_val = sc->cval; ta.cand_idx = sc->cidx;

@@ -188,7 +188,7 @@ static int learned_search(wh_stream* s) {
 
 static void fill_tc_args(const wh_stream* s, AutocorrTcArgs& ta) {
   ta.H = s->H; ta.W = s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad; ta.kg = s->kg;
-  ta.ntile = s->ntile; ta.mode = s->tc_mode; ta.bf16 = s->tc_bf16;
+  ta.ntile = s->ntile; ta.ncand = 8; ta.ovf_group = 8; ta.mode = s->tc_mode; ta.bf16 = s->tc_bf16;
   ta.vmax = float(s->vmax); ta.vstep = float(s->vstep); ta.Astate = s->Astate;
   ta.a16 = s->d_a16; ta.l1 = s->d_l1; ta.cand_val = s->d_cval; ta.cand_idx = s->d_cidx;
   ta.vidx = s->vidx; ta.vx = s->vx; ta.vy = s->vy; ta.tab_x = s->d_tabx; ta.n_fallback = s->d_nfb;
@@ -346,8 +346,9 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   if (s->use_tc) {
     alloc((void**)&s->d_a16, 2 * npix * s->kg);
     alloc((void**)&s->d_l1, sizeof(float) * npix);
-    alloc((void**)&s->d_cval, sizeof(float) * npix * s->ntile * 4);
-    alloc((void**)&s->d_cidx, sizeof(int) * npix * s->ntile * 4);
+    const size_t nc = size_t(s->ntile * 4 > 8 ? s->ntile * 4 : 8);
+    alloc((void**)&s->d_cval, sizeof(float) * npix * nc);
+    alloc((void**)&s->d_cidx, sizeof(int) * npix * nc);
     alloc((void**)&s->d_table, 2 * size_t(s->ntile) * 128 * s->kg);
     alloc((void**)&s->d_err, sizeof(int));
     alloc((void**)&s->d_nfb, sizeof(int));
@@ -466,11 +467,9 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
     fill_tc_args(s, ta);
     e = launch_autocorr_convert(ta, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation convert kernel");
-    GemmArgs g{};
-    g.M = s->H * s->W; g.N = s->ntile * 128; g.K = s->M * s->M; g.bf16 = s->tc_bf16;
-    g.epi = EPI_TOPK; g.cand_val = s->d_cval; g.cand_idx = s->d_cidx; g.n_valid = s->L * s->L;
-    g.err = s->d_err;
-    e = tc_gemm(g, s->d_a16, s->kg, s->d_table, s->kg, 128, s->st);
+    e = tc_autocorr_shortlist(s->d_a16, s->kg, s->d_table, s->kg, s->H * s->W, s->M * s->M, s->ntile,
+                              s->L * s->L, s->tc_bf16 != 0, s->tc_mode == 0 ? s->d_l1 : nullptr,
+                              s->d_cval, s->d_cidx, s->d_err, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "tensor-core autocorrelation");
     e = launch_autocorr_rerank(ta, s->st);
     if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation re-rank kernel");

@@ -230,6 +230,10 @@ cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, 
 
 }  // namespace
 
+bool make_map_2b(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int box_rows, bool bf16) {
+  return make_map(m, ptr, rows, K, ld, box_rows, bf16);
+}
+
 cudaError_t tc_gemm(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, int bn,
                     cudaStream_t st) {
   if (g.M < 1 || g.N < 1 || g.K < 1 || !g.err) return cudaErrorInvalidValue;

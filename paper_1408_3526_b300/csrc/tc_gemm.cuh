@@ -27,4 +27,13 @@ struct GemmArgs {
 cudaError_t tc_gemm(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, int bn,
                     cudaStream_t st);
 
+// Persistent autocorrelation shortlist (tc_rgemm.cu): per row of a16 [M][lda]
+// (K <= 256), the 8 largest a16 . table[l] over l < n_valid, table
+// [ntile*128][ldb]; candidates cval/cidx [M][8].  With l1 (per-row sum |a16|)
+// given, values more than the re-rank's window below their 32-column chunk's
+// maximum are skipped (they cannot matter to the exact re-rank).
+cudaError_t tc_autocorr_shortlist(const void* a16, int lda, const void* table, int ldb, int M, int K,
+                                  int ntile, int n_valid, bool bf16, const float* l1, float* cval,
+                                  int* cidx, int* err, cudaStream_t st);
+
 }  // namespace wh
