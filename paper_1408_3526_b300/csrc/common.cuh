@@ -121,6 +121,18 @@ __host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(
 __host__ __device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __host__ __device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
+// Output-tile width of the spectrum kernel for window M and temporal order Mz:
+// the largest TW with TW + 2K <= 32 (one observer lane per input pixel of the
+// row segment) and TW * (y-SDFT channels), rounded to warps, plus the observer
+// warp within 384 threads (two CTAs per SM).
+__host__ __device__ constexpr int spec_tile_w(int M, int Mz) {
+  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
+  const int nchy = ((Mz % 2) == 0 ? 2 : 1) * (K + 1) + J * M;
+  int tw = 32 - 2 * K;
+  while (tw > 1 && ((tw * nchy + 31) / 32) * 32 + 32 > 384) --tw;
+  return tw;
+}
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st);
@@ -128,6 +140,8 @@ cudaError_t launch_pef(const PefArgs& a, cudaStream_t st);
 cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
 bool spectrum_supported(int M, int Mz);
 cudaError_t spectrum_init_constants();
+int spectrum_threads(int M, int Mz);      // block size of the spectrum kernel
+size_t spectrum_smem(int M, int Mz);      // its dynamic shared memory (bytes)
 bool autocorr_tc_supported(int M);
 cudaError_t launch_autocorr_convert(const AutocorrTcArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr_rerank(const AutocorrTcArgs& a, cudaStream_t st);

@@ -16,19 +16,26 @@
 // smoother R'_t = (1-alpha) R_t + alpha R'_{t-1} is linear, so it is applied
 // to the M^2 numbers A instead of the L^2 values of R (identical result).
 //
-// Organisation: one CTA owns a strip of TW output columns x TH output rows and
-// walks down it one input row at a time (TH + 2K rows, clamped at the frame
-// edge):
-//   A  observer update of the row segment (TW + 2K pixels), Hann along kz;
-//   B  x-DFT of the row: every (channel, column) as a direct M-tap sum with the
-//      Hann(x) window and the centring phase folded into its weights;
+// Organisation: one CTA owns a strip of TW output columns and walks down its
+// share of rows one input row at a time (2K halo rows first); all geometry is
+// fixed at compile time by (M, Mz).  Per input row:
+//   A  (observer warp) observer update of the TW + 2K pixels of the row, Hann
+//      along kz, and the M-pixel box sums along x of every plane (warp
+//      shuffles) with their running sum over the last M rows, which is the
+//      removed (0,0) bin that the high-pass correction needs;
+//   B  x-DFT units (x, kx >= 0, plane group): a direct M-tap sum with the
+//      Hann(x) window, the centring phase and the power scale folded into the
+//      weights; a complex plane's +kx and -kx outputs come from the same four
+//      accumulators (the -kx weights are the conjugates);
 //   C  y-SDFT: one thread per (channel, column) carries the M ky-resonators
-//      of that column (comb input from a ring of the last M+1 x-DFT rows),
-//      then Hann along ky (real 3 taps in the centred basis), the high-pass
-//      correction and the power of the output row;
-//   D  per output pixel, reduce P over kz into A, smooth, store.
-// Register prefetch hides the HBM latency of the next row's frame/observer
-// state (phase A) and of the next output row's smoother state (phase D).
+//      (comb input from a ring of the last M+1 x-DFT rows), then Hann along ky
+//      (real 3 taps in the centred basis), the high-pass correction and the
+//      power of the output row;
+//   D  per (output pixel, h): the kz reduction into A_c/A_s read at fixed
+//      offsets of the power block (+-h plus constants, no index table), the
+//      smoother update and the store; the next row's smoother state is
+//      prefetched with cp.async.
+// Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1)}.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -39,26 +46,74 @@ namespace wh {
 
 namespace {
 
-constexpr int kPrefA = kMaxMz + 1;   // frame + Mz state floats per phase-A pixel
-constexpr int kMaxDTasks = 4;        // phase-D tasks per thread (checked on the host)
-constexpr int kSpecMaxThreads = 384;   // y-SDFT threads rounded to warps + one observer warp
-constexpr int kMaxBTasks = 2;        // phase-B tasks per thread (checked on the host)
+constexpr int kZN = kMaxMz - 2;     // temporal orders Mz = 3 .. kMaxMz
 
+// Resonator twiddles e^{+j2pi ky/M} and centring phases e^{-j2pi ky K/M} per
+// window size (index (M-3)/2, ky+K); observer rotations, Hann(kz) phase and
+// the kz reduction's cos/sin per temporal order (index Mz-3).  Indexed at
+// compile time in the kernel, so they are read as constant-bank operands.
+__constant__ float2 c_wres[7][kMaxM];
+__constant__ float2 c_cph[7][kMaxM];
+__constant__ float2 c_lam[kZN][kMaxPlanes];
+__constant__ float2 c_hz[kZN];
+__constant__ float c_cz[kZN][kMaxPlanes];
+__constant__ float c_sz[kZN][kMaxPlanes];
+
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// Compile-time geometry of one (M, Mz) configuration.
 template <int M, int MZ>
-struct Geo {
+struct SG {
   static constexpr int K = (M - 1) / 2;
-  static constexpr int J = (MZ - 1) / 2;                 // complex planes 1..J
+  static constexpr int J = (MZ - 1) / 2;                  // complex planes 1..J
   static constexpr bool EVEN = (MZ % 2) == 0;
-  static constexpr int NPL = J + 1 + (EVEN ? 1 : 0);     // stored planes
+  static constexpr int NREAL = EVEN ? 2 : 1;              // real planes 0 (and Mz/2)
+  static constexpr int NPL = J + NREAL;                   // stored planes
+  static constexpr int NCHY = NREAL * (K + 1) + J * M;    // y-SDFT channels
+  static constexpr int NH = (M * M - 1) / 2;
+  static constexpr int NH1 = NH + 1;
+  static constexpr int TW = spec_tile_w(M, MZ);
+  static constexpr int RW = TW + 2 * K;
+  static constexpr int NCT = TW * NCHY;                   // y-SDFT threads
+  static constexpr int NTHR = cdiv(NCT, 32) * 32 + 32;    // + the observer warp
+  static constexpr int PS = (NCHY * M) | 1;               // odd pixel stride of pbuf
+  static constexpr int KPAD = (M * M + 3) & ~3;
+  // x-DFT units (group, kx, x), group 0 = the real planes, j = complex plane j;
+  // each group padded to whole warps so a warp runs one code path
+  static constexpr int GU = TW * (K + 1);
+  static constexpr int GP = cdiv(GU, 32) * 32;
+  static constexpr int NBT = (J + 1) * GP;                // x-DFT threads
+  static constexpr int NDT = TW * NH1;                    // reduction tasks per row
+  // Reduction on the warps without x-DFT work, or on all warps, whichever has
+  // the shorter estimated critical path (x-DFT unit ~7 instr/tap, task ~28).
+  static constexpr int BCOST = 7 * M + 12, DCOST = 28;
+  static constexpr int SPLIT_COST =
+      (NBT < NTHR) ? imax(BCOST, cdiv(NDT, NTHR - NBT) * DCOST) : (1 << 30);
+  static constexpr int ALL_COST = BCOST + cdiv(NDT, NTHR) * DCOST;
+  static constexpr int D0 = SPLIT_COST <= ALL_COST ? NBT : 0;   // first reduction thread
+  static constexpr int NDTHR = NTHR - D0;
+  static constexpr int QD = cdiv(NDT, NDTHR);             // reduction rounds per row
+  // first channel of plane p (channel order: plane 0 kx = 0..K, complex planes
+  // kx = -K..K, Nyquist plane kx = 0..K)
+  __host__ __device__ static constexpr int base(int p) { return p == 0 ? 0 : (K + 1) + (p - 1) * M; }
+  // shared-memory layout (bytes)
+  static constexpr size_t O_TWR = 0;                                           // float2 [NPL][RW]
+  static constexpr size_t O_RING = al16(O_TWR + 8ull * NPL * RW);              // float2 [M+1][NCHY][TW]
+  static constexpr size_t O_DCR = al16(O_RING + 8ull * (M + 1) * NCHY * TW);   // float2 [M+1][NPL][TW]
+  static constexpr size_t O_XW = al16(O_DCR + 8ull * (M + 1) * NPL * TW);      // float2 [K+1][M]
+  static constexpr size_t O_PBUF = al16(O_XW + 8ull * (K + 1) * M);            // float  [TW][PS]
+  static constexpr size_t O_DBUF = al16(O_PBUF + 4ull * TW * PS);              // float2 [2][NPL][TW]
+  static constexpr size_t O_ABUF = al16(O_DBUF + 8ull * 2 * NPL * TW);         // float  [RW][MZ+1]
+  static constexpr size_t O_DPRE = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [QD][2][NDTHR]
+  static constexpr size_t O_OFFS = al16(O_DPRE + 4ull * QD * 2 * NDTHR);       // float2 [NPL]
+  static constexpr size_t SMEM = al16(O_OFFS + 8ull * NPL);
+  static_assert(RW <= 32, "the observer warp covers the row segment");
+  static_assert(NBT <= NTHR, "one x-DFT unit per thread");
 };
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
-
-// Resonator twiddles e^{+j2pi ky/M} and centring phases e^{-j2pi ky K/M} per
-// window size (index (M-3)/2, ky+K); indexed at compile time in the kernel, so
-// they are read as constant-bank operands.
-__constant__ float2 c_wres[7][kMaxM];
-__constant__ float2 c_cph[7][kMaxM];
 
 // Per-thread asynchronous 4-byte copies global -> shared (each thread later
 // consumes only what it copied, so a wait on its own groups suffices).
@@ -67,55 +122,34 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__host__ __device__ inline int spec_threads_for(int M, int Mz, int tw) {
-  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
-  const int nchy = (1 + ((Mz % 2) == 0 ? 1 : 0)) * (K + 1) + J * M;
-  return ((tw * nchy + 31) / 32) * 32 + 32;      // + the observer warp
-}
-
-// Byte offsets of the shared-memory arrays (16-byte aligned each); the same
-// function sizes the launch on the host.
-struct SpecSmem {
-  size_t twr, ring, xc, pbuf, hg, wres, cph, off, dbuf, abuf, dpre, total;
-};
-__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
-__host__ __device__ inline SpecSmem spec_smem_layout(int M, int Mz, int tw) {
-  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
-  const bool even = (Mz % 2) == 0;
-  const int npl = J + 1 + (even ? 1 : 0);
-  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
-  const int nch = nchy + npl;
-  const int nh = (M * M - 1) / 2;
-  const int nslot = 1 + 2 * J + (even ? 1 : 0);
-  const int PS = (nchy * M) | 1;
-  const int RW = tw + 2 * K;
-  SpecSmem L;
-  size_t o = 0;
-  L.twr = o;  o = align16(o + sizeof(float2) * size_t(npl) * RW);
-  L.ring = o; o = align16(o + sizeof(float2) * size_t(M + 1) * nch * tw);
-  L.xc = o;   o = align16(o + sizeof(float2) * size_t(nch) * M);
-  L.pbuf = o; o = align16(o + sizeof(float) * size_t(tw) * PS);
-  L.hg = o;   o = align16(o + sizeof(int) * size_t(nh + 1) * nslot);
-  L.wres = o; o = align16(o + sizeof(float2) * M);
-  L.cph = o;  o = align16(o + sizeof(float2) * M);
-  L.off = o;  o = align16(o + sizeof(float2) * npl);
-  L.dbuf = o; o = align16(o + sizeof(float2) * size_t(npl) * tw);
-  L.abuf = o; o = align16(o + sizeof(float) * size_t(RW) * kPrefA);
-  L.dpre = o; o = align16(o + sizeof(float) * size_t(kMaxDTasks) * 2 * spec_threads_for(M, Mz, tw));
-  L.total = o;
-  return L;
+// Sum of M consecutive lanes' values starting at this lane (lanes + M - 1 <= 31
+// are exact; the rest are unused), by doubling windows.
+template <int M>
+__device__ __forceinline__ float lane_box_sum(float v) {
+  static_assert(M < 16, "window");
+  const unsigned full = 0xffffffffu;
+  const float s1 = v;
+  const float s2 = s1 + __shfl_down_sync(full, s1, 1);
+  const float s4 = s2 + __shfl_down_sync(full, s2, 2);
+  const float s8 = s4 + __shfl_down_sync(full, s4, 4);
+  float r = 0.f;
+  int off = 0;
+  if (M & 8) { r = s8; off = 8; }
+  if (M & 4) { r += off ? __shfl_down_sync(full, s4, off) : s4; off += 4; }
+  if (M & 2) { r += off ? __shfl_down_sync(full, s2, off) : s2; off += 2; }
+  if (M & 1) { r += off ? __shfl_down_sync(full, s1, off) : s1; }
+  return r;
 }
 
 // Observer update of one pixel (frame value pa[0], packed T_{t-1} in pa[1..Mz])
-// -> T_t (packed, written back into T) and its Hann-windowed planes Tw.
+// -> T_t (packed) and its Hann-windowed planes Tw.
 template <int M, int MZ>
-__device__ __forceinline__ void observer_hann(const float* pa, const float2* lam, float2 hz,
-                                              float2 (&T)[Geo<M, MZ>::NPL],
-                                              float2 (&Tw)[Geo<M, MZ>::NPL]) {
-  using G = Geo<M, MZ>;
-  constexpr int J = G::J, NPL = G::NPL;
+__device__ __forceinline__ void observer_hann(const float* pa, float2 (&T)[SG<M, MZ>::NPL],
+                                              float2 (&Tw)[SG<M, MZ>::NPL]) {
+  using G = SG<M, MZ>;
+  constexpr int J = G::J, NPL = G::NPL, ZI = MZ - 3;
   constexpr bool EVEN = G::EVEN;
   const float xin = pa[0];
   T[0] = make_float2(pa[1], 0.f);
@@ -127,7 +161,7 @@ __device__ __forceinline__ void observer_hann(const float* pa, const float2* lam
   float yhat = 0.f;
 #pragma unroll
   for (int p = 0; p < NPL; ++p) {
-    s[p] = cmul(lam[p], T[p]);
+    s[p] = cmul(c_lam[ZI][p], T[p]);
     const bool real = (p == 0) || (EVEN && p == NPL - 1);
     yhat += real ? s[p].x : 2.f * s[p].x;
   }
@@ -139,6 +173,7 @@ __device__ __forceinline__ void observer_hann(const float* pa, const float2* lam
     if (real) T[p].y = 0.f;
   }
   // Hann along kz: Tw(p) = 1/2 T(p) + 1/4 hz T(p+1) + 1/4 conj(hz) T(p-1), bins mod Mz
+  const float2 hz = c_hz[ZI];
   float2 Tf[MZ];
   Tf[0] = T[0];
 #pragma unroll
@@ -155,68 +190,55 @@ __device__ __forceinline__ void observer_hann(const float* pa, const float2* lam
   }
 }
 
-template <int M, int MZ>
-__global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const SpecArgs a) {
-  using G = Geo<M, MZ>;
-  constexpr int K = G::K, J = G::J, NPL = G::NPL;
+template <int M, int MZ, bool DUMP>
+__global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const SpecArgs a) {
+  using G = SG<M, MZ>;
+  constexpr int K = G::K, J = G::J, NPL = G::NPL, NCHY = G::NCHY;
+  constexpr int TW = G::TW, RW = G::RW, NTHR = G::NTHR, PS = G::PS, KPAD = G::KPAD;
+  constexpr int NH = G::NH, NH1 = G::NH1, NDT = G::NDT, NDTHR = G::NDTHR, D0 = G::D0, QD = G::QD;
   constexpr bool EVEN = G::EVEN;
-  const SpecTables& tb = *a.tables;
-  const int TW = a.tw, H = a.H, W = a.W;
-  const int RW = TW + 2 * K;
-  const int nch = tb.nch, nchy = tb.nchy, nh = tb.nh, nslot = tb.nslot;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int PS = (nchy * M) | 1;                          // odd pixel stride of pbuf
+  constexpr int MI = (M - 3) / 2, ZI = MZ - 3;
+  constexpr int RING_SLOT = NCHY * TW, DC_SLOT = NPL * TW;
+  const int H = a.H, W = a.W;
+  const int tid = threadIdx.x, lane = tid & 31;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SpecSmem SL = spec_smem_layout(M, MZ, TW);
-  float2* twr = reinterpret_cast<float2*>(smem_raw + SL.twr);         // [NPL][RW]
-  float2* ring = reinterpret_cast<float2*>(smem_raw + SL.ring);       // [M+1][nch][TW]
-  float2* xc = reinterpret_cast<float2*>(smem_raw + SL.xc);           // [nch][M]
-  float* pbuf = reinterpret_cast<float*>(smem_raw + SL.pbuf);         // [TW][PS]
-  int* hg = reinterpret_cast<int*>(smem_raw + SL.hg);                 // [(nh+1)][nslot]
-  float2* offs = reinterpret_cast<float2*>(smem_raw + SL.off);        // [NPL]
-  float2* dbuf = reinterpret_cast<float2*>(smem_raw + SL.dbuf);       // [NPL][TW]
-  float* abuf = reinterpret_cast<float*>(smem_raw + SL.abuf);         // [RW][kPrefA]
-  float* dpre = reinterpret_cast<float*>(smem_raw + SL.dpre);         // [kMaxDTasks][2][nthr]
-  constexpr int MI = (M - 3) / 2;
+  float2* twr = reinterpret_cast<float2*>(smem_raw + G::O_TWR);
+  float2* ring = reinterpret_cast<float2*>(smem_raw + G::O_RING);
+  float2* dcr = reinterpret_cast<float2*>(smem_raw + G::O_DCR);
+  float2* xw = reinterpret_cast<float2*>(smem_raw + G::O_XW);
+  float* pbuf = reinterpret_cast<float*>(smem_raw + G::O_PBUF);
+  float2* dbuf = reinterpret_cast<float2*>(smem_raw + G::O_DBUF);
+  float* abuf = reinterpret_cast<float*>(smem_raw + G::O_ABUF);
+  float* dpre = reinterpret_cast<float*>(smem_raw + G::O_DPRE);
+  float2* offs = reinterpret_cast<float2*>(smem_raw + G::O_OFFS);
 
-  for (int i = tid; i < nch * M; i += nthr) xc[i] = tb.xcoef[i / M][i % M];
-  for (int i = tid; i < (nh + 1) * nslot; i += nthr) hg[i] = a.hgather[i];
-  float2 lam[NPL];
-#pragma unroll
-  for (int p = 0; p < NPL; ++p) lam[p] = tb.lam[p];
-  const float2 hz = tb.hann_z;
+  // Power scale (Mz/sqrt(N))^2 and the 1/16 of the 4x Hann taps, as sig^2 on
+  // the x-DFT weights and box sums (everything before the power is linear).
+  const float sig = sqrtf(float(MZ) / float(16 * M * M));
+  for (int i = tid; i < (K + 1) * M; i += NTHR) xw[i] = cscale(a.tables->xcoef[i / M][i % M], sig);
   const float alpha = a.alpha, oma = 1.0f - alpha;
-  const float sP = float(MZ) * float(MZ) / float(M * M * MZ);   // (Mz/sqrt(N))^2
 
-  // ---- static task assignment (identical for every row) -----------------------
-  // B: (channel, column) x-DFT tasks, packed: c | x << 8 | plane << 16 | real << 20 | dc << 21
-  int btask[kMaxBTasks];
-#pragma unroll
-  for (int q = 0; q < kMaxBTasks; ++q) {
-    const int task = tid + q * nthr;
-    if (task < nch * TW) {
-      const int c = task / TW, x = task % TW, p = tb.ch_plane[c];
-      const int real = (p == 0) || (EVEN && p == NPL - 1);
-      btask[q] = c | (x << 8) | (p << 16) | (real << 20) | (int(c >= nchy) << 21);
-    } else {
-      btask[q] = -1;
-    }
-  }
-  // C: one (channel, column) y-SDFT per thread
-  const bool yth = tid < TW * nchy;
-  const int cy = yth ? tid / TW : 0;
-  const int xy = yth ? tid % TW : 0;
-  const int kxc = tb.ch_kx[cy];
-  const int plc = tb.ch_plane[cy];
-  // D: (pixel column, h) reduction tasks, packed: hi | x << 16
-  const int ntD = TW * (nh + 1);
-  int dtask[kMaxDTasks];
-#pragma unroll
-  for (int q = 0; q < kMaxDTasks; ++q) {
-    const int task = tid + q * nthr;
-    dtask[q] = task < ntD ? ((task % (nh + 1)) | ((task / (nh + 1)) << 16)) : -1;
-  }
+  // ---- static roles ---------------------------------------------------------
+  // C: y-SDFT channel cy (plane plc, kx kxc) of column xy
+  const bool cthr = tid < G::NCT;
+  const int cy = cthr ? tid / TW : 0, xy = cthr ? tid % TW : 0;
+  int plc, kxc;
+  if (cy < K + 1) { plc = 0; kxc = cy; }
+  else if (cy < K + 1 + J * M) { plc = 1 + (cy - (K + 1)) / M; kxc = (cy - (K + 1)) % M - K; }
+  else { plc = NPL - 1; kxc = cy - (K + 1) - J * M; }
+  const float wxh = kxc == 0 ? 0.5f : ((kxc == 1 || kxc == -1) ? 0.25f : 0.f);
+  // B: x-DFT unit (group bg, kx bkx, column bx)
+  const int bg = tid / G::GP, br = tid % G::GP;
+  const bool bthr = tid < G::NBT && br < G::GU;
+  const int bkx = br / TW, bx = br % TW;
+  // A: observer lane ua of the last warp
+  const bool owarp = tid >= NTHR - 32;
+  const int ua = lane;
+  const bool athr = owarp && ua < RW;
+  // D: reduction thread index
+  const bool dthr = tid >= D0;
+  const int dt = tid - D0;
 
   // ---- this CTA's share of the (strip, row) units -------------------------------
   const int nstrip = (W + TW - 1) / TW;
@@ -231,108 +253,136 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     const int y1 = int(min((long long)H, (long long)y0 + (u1 - u)));
     u += y1 - y0;
     const int x0 = strip * TW;
-    const int TH = y1 - y0;
+    const int nrows = y1 - y0 + 2 * K;
 
     float2 Y[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) Y[k] = make_float2(0.f, 0.f);
-    float2 drun[kMaxBTasks];
-#pragma unroll
-    for (int q = 0; q < kMaxBTasks; ++q) drun[q] = make_float2(0.f, 0.f);
-    const int nrows = TH + 2 * K;
 
-    // The last warp runs the observer update of the next input row while the
-    // other warps run the y-recursion of the current one.
-    const int ua = tid - (nthr - 32);
-    const bool athr = ua >= 0 && ua < RW;
-    float pa[kPrefA];
     auto loadA = [&](int i) {             // prefetch input row i into this lane's abuf slot
       if (athr) {
         const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + ua, W);
         const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
-        float* dst = abuf + ua * kPrefA;
+        float* dst = abuf + ua * (MZ + 1);
         cp_async4(dst, a.frame + o);
 #pragma unroll
         for (int f = 0; f < MZ; ++f) cp_async4(dst + 1 + f, a.obs_old + f * plane + o);
       }
       cp_async_commit();
     };
-    auto doA = [&](int i) {               // observer update + Hann(kz) of input row i
-      if (!athr) return;
+    auto doA = [&](int i) {               // whole observer warp: observer, Hann(kz), box sums
       const int r = y0 - K + i;
+      float2 v[NPL];
+      if (athr) {
+        float pa[MZ + 1];
 #pragma unroll
-      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[ua * kPrefA + f];
-      float2 T[NPL], Tw[NPL];
-      observer_hann<M, MZ>(pa, lam, hz, T, Tw);
-      const int xs = x0 - K + ua;
-      if (r >= y0 && r < y1 && ua >= K && ua < K + TW && xs < W) {   // owner writes the new state
-        const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
-        a.obs_new[o] = T[0].x;
+        for (int f = 0; f <= MZ; ++f) pa[f] = abuf[ua * (MZ + 1) + f];
+        float2 T[NPL], Tw[NPL];
+        observer_hann<M, MZ>(pa, T, Tw);
+        const int xs = x0 - K + ua;
+        if (r >= y0 && r < y1 && ua >= K && ua < K + TW && xs < W) {   // owner writes the new state
+          const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
+          a.obs_new[o] = T[0].x;
 #pragma unroll
-        for (int j = 1; j <= J; ++j) {
-          a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
-          a.obs_new[(2 * j) * plane + o] = T[j].y;
+          for (int j = 1; j <= J; ++j) {
+            a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
+            a.obs_new[(2 * j) * plane + o] = T[j].y;
+          }
+          if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
         }
-        if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) {
+          v[p] = csub(Tw[p], offs[p]);
+          twr[p * RW + ua] = v[p];
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) v[p] = make_float2(0.f, 0.f);
       }
+      // box sums along x (the (0,0) bin of the row window at column ua), their
+      // running sum over the last M rows, and a ring of the last M+1 rows' sums
+      float2 bs[NPL];
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) twr[p * RW + ua] = csub(Tw[p], offs[p]);
+      for (int p = 0; p < NPL; ++p) {
+        const bool real = (p == 0) || (EVEN && p == NPL - 1);
+        bs[p].x = lane_box_sum<M>(v[p].x);
+        bs[p].y = real ? 0.f : lane_box_sum<M>(v[p].y);
+      }
+      if (ua < TW) {
+        const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);   // oslot holds row i - M
+        float2* dnew = dbuf + (i & 1) * DC_SLOT;
+        const float2* dold = dbuf + ((i + 1) & 1) * DC_SLOT;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) {
+          const float2 val = cscale(bs[p], sig);
+          float2 run = i > 0 ? cadd(dold[p * TW + ua], val) : val;
+          if (i >= M) run = csub(run, dcr[oslot * DC_SLOT + p * TW + ua]);
+          dcr[slot * DC_SLOT + p * TW + ua] = val;
+          dnew[p * TW + ua] = run;
+        }
+      }
     };
-    // phase-D prefetch of the smoother state of an output row (own slots of dpre)
+    // phase-D prefetch of the smoother state of output row yo (own slots of dpre)
     auto loadD = [&](int yo) {
+      if (dthr && yo < y1) {
+        const float* rowA = a.Astate + (size_t(yo) * W + x0) * KPAD;
 #pragma unroll
-      for (int q = 0; q < kMaxDTasks; ++q) {
-        const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
-        if (dtask[q] >= 0 && yo < y1 && x0 + x < W) {
-          const float* src = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-          cp_async4(dpre + (q * 2 + 0) * nthr + tid, src + hi);
-          if (hi > 0) cp_async4(dpre + (q * 2 + 1) * nthr + tid, src + nh + hi);
+        for (int q = 0; q < QD; ++q) {
+          const int d = dt + q * NDTHR;
+          if (d >= NDT) break;
+          const int x = d / NH1, hi = d - x * NH1;
+          if (x0 + x >= W) continue;
+          const float* src = rowA + x * KPAD + hi;
+          cp_async4(dpre + (2 * q) * NDTHR + dt, src);
+          if (hi > 0) cp_async4(dpre + (2 * q + 1) * NDTHR + dt, src + NH);
         }
       }
       cp_async_commit();
     };
     auto doB = [&](int i) {               // x-DFT of input row i into ring slot i mod (M+1)
-      const int slot = i % (M + 1);
-      const int oslot = (i + 1) % (M + 1);    // holds row i - M
+      if (!bthr) return;
+      float2* rs = ring + (i % (M + 1)) * RING_SLOT;
+      const float2* w = xw + bkx * M;
+      if (bg == 0) {                      // real planes: real data, complex weights
+        const float2* r0 = twr + bx + 2 * K;
+        const float2* r1 = twr + (NPL - 1) * RW + bx + 2 * K;
+        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < kMaxBTasks; ++q) {
-        const int bt = btask[q];
-        if (bt < 0) continue;
-        const int c = bt & 0xff, x = (bt >> 8) & 0xff, pl = (bt >> 16) & 0xf;
-        const float2* row = twr + pl * RW + x + 2 * K;       // u = x + 2K - mx
-        const float2* w = xc + c * M;
-        float2 acc = make_float2(0.f, 0.f);
-        if (bt & (1 << 20)) {
-#pragma unroll
-          for (int mx = 0; mx < M; ++mx) {
-            const float v = row[-mx].x;
-            const float2 cw = w[mx];
-            acc.x = fmaf(cw.x, v, acc.x);
-            acc.y = fmaf(cw.y, v, acc.y);
-          }
-        } else {
-#pragma unroll
-          for (int mx = 0; mx < M; ++mx) {
-            const float2 v = row[-mx], cw = w[mx];
-            acc.x = fmaf(cw.x, v.x, fmaf(-cw.y, v.y, acc.x));
-            acc.y = fmaf(cw.x, v.y, fmaf(cw.y, v.x, acc.y));
+        for (int mx = 0; mx < M; ++mx) {
+          const float2 cw = w[mx];
+          const float v0 = r0[-mx].x;
+          c0.x = fmaf(cw.x, v0, c0.x);
+          c0.y = fmaf(cw.y, v0, c0.y);
+          if (EVEN) {
+            const float v1 = r1[-mx].x;
+            c1.x = fmaf(cw.x, v1, c1.x);
+            c1.y = fmaf(cw.y, v1, c1.y);
           }
         }
-        if (bt & (1 << 21)) {                  // running box sum for the high-pass
-          drun[q] = cadd(drun[q], acc);
-          if (i >= M) drun[q] = csub(drun[q], ring[(oslot * nch + c) * TW + x]);
-          dbuf[pl * TW + x] = drun[q];
+        rs[bkx * TW + bx] = c0;                                   // channel (0, kx)
+        if (EVEN) rs[(G::base(NPL - 1) + bkx) * TW + bx] = c1;    // channel (Mz/2, kx)
+      } else {                            // complex plane bg: +kx and -kx together
+        const float2* row = twr + bg * RW + bx + 2 * K;
+        float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
+#pragma unroll
+        for (int mx = 0; mx < M; ++mx) {
+          const float2 cw = w[mx], v = row[-mx];
+          pa = fmaf(cw.x, v.x, pa);
+          pb = fmaf(cw.y, v.y, pb);
+          pc = fmaf(cw.x, v.y, pc);
+          pd = fmaf(cw.y, v.x, pd);
         }
-        ring[(slot * nch + c) * TW + x] = acc;
+        const int c0 = G::base(bg) + K;                           // channel (bg, 0)
+        rs[(c0 + bkx) * TW + bx] = make_float2(pa - pb, pc + pd);
+        if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_float2(pa + pb, pc - pd);
       }
     };
     auto doC = [&](int i) {               // y-SDFT, Hann(ky), high-pass, power of row i
-      if (!yth) return;
-      const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);
+      if (!cthr) return;
       const int yo = y0 + i - 2 * K;
-      const float2 xn = ring[(slot * nch + cy) * TW + xy];
+      const float2 xn = ring[(i % (M + 1)) * RING_SLOT + tid];
       float2 d = xn;
-      if (i >= M) d = csub(xn, ring[(oslot * nch + cy) * TW + xy]);
+      if (i >= M) d = csub(xn, ring[((i + 1) % (M + 1)) * RING_SLOT + tid]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         const float2 w = c_wres[MI][k], c = c_cph[MI][k];
@@ -341,29 +391,23 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
       }
       if (!(i >= 2 * K && yo < y1)) return;
       // 4 x [Hann along ky (taps 1/4, 1/2, 1/4 in the centred basis), minus
-      // Hann_x Hann_y of the removed (0,0) bin]; the factor 16 is in the power scale
-      float2 D = make_float2(0.f, 0.f);
-      float wxh = 0.f;
-      if (kxc >= -1 && kxc <= 1) {
-        D = dbuf[plc * TW + xy];
-        wxh = (kxc == 0) ? 0.5f : 0.25f;
-      }
+      // Hann_x Hann_y of the removed (0,0) bin]; the 1/16 is in sig^2
+      const float2 D = dbuf[(i & 1) * DC_SLOT + plc * TW + xy];
       float* pb = pbuf + xy * PS + cy * M;
-      const bool dump = (a.dump_win != nullptr) && (x0 + xy < W);
-      const float sP16 = sP * (1.f / 16.f);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         float2 z = cadd(cscale(Y[k], 2.f), cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]));
         if (k == K) z = csub(z, cscale(D, wxh * 2.f));
         if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh));
-        const float pw = sP16 * fmaf(z.x, z.x, z.y * z.y);
+        const float pw = fmaf(z.x, z.x, z.y * z.y);
         pb[k] = pw;
-        if (dump) {
+        if (DUMP && x0 + xy < W) {
           // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
+          const SpecTables& tb = *a.tables;
           const size_t pix = size_t(yo) * W + x0 + xy;
           const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
           const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
-                                   0.25f * float(MZ) / sqrtf(float(M * M * MZ)));
+                                   0.25f * float(MZ) / sqrtf(float(M * M * MZ)) / sig);
           const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
           const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
           a.dump_win[op] = sv;
@@ -374,32 +418,38 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     };
     auto doD = [&](int i) {               // reduce over kz, smooth, store (output row of i)
       const int yo = y0 + i - 2 * K;
-      if (!(i >= 2 * K && yo < y1)) return;
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      if (!(i >= 2 * K && yo < y1) || !dthr) return;
+      cp_async_wait0();
+      float* rowA = a.Astate + (size_t(yo) * W + x0) * KPAD;
 #pragma unroll
-      for (int q = 0; q < kMaxDTasks; ++q) {
-        const int x = dtask[q] >> 16, hi = dtask[q] & 0xffff;
-        if (dtask[q] < 0 || x0 + x >= W) continue;
-        const int* g = hg + hi * nslot;
-        const float* pb = pbuf + x * PS;
-        float Ac = pb[g[0]], As = 0.f;
+      for (int q = 0; q < QD; ++q) {
+        const int d = dt + q * NDTHR;
+        if (d >= NDT) break;
+        const int x = d / NH1, hi = d - x * NH1;
+        if (x0 + x >= W) continue;
+        // P(h, kz) for the slots kz = 0, +j, -j (= P(-h, +j)), Mz/2 of this h:
+        // offsets x*PS + (c*M + ky + K) with c the channel of (plane, +-hx)
+        const int op = x * PS + hi + K, om = x * PS - hi + K;
+        float Ac = pbuf[op], As = 0.f;
 #pragma unroll
         for (int j = 1; j <= J; ++j) {
-          const float pp = pb[g[j]], pm = pb[g[J + j]];
-          Ac = fmaf(pp + pm, tb.cz[j], Ac);
-          As = fmaf(pp - pm, tb.sz[j], As);
+          const float pp = pbuf[op + (G::base(j) + K) * M], pm = pbuf[om + (G::base(j) + K) * M];
+          Ac = fmaf(pp + pm, c_cz[ZI][j], Ac);
+          As = fmaf(pp - pm, c_sz[ZI][j], As);
         }
-        if (EVEN) Ac -= pb[g[2 * J + 1]];
-        float* dst = a.Astate + (size_t(yo) * W + x0 + x) * a.kpad;
-        dst[hi] = fmaf(oma, Ac, alpha * dpre[(q * 2 + 0) * nthr + tid]);
-        if (hi > 0) dst[nh + hi] = fmaf(oma, As, alpha * dpre[(q * 2 + 1) * nthr + tid]);
+        if (EVEN) Ac -= pbuf[op + G::base(NPL - 1) * M];
+        float* dst = rowA + x * KPAD + hi;
+        const float* pre = dpre + (2 * q) * NDTHR + dt;
+        dst[0] = fmaf(oma, Ac, alpha * pre[0]);
+        if (hi > 0) dst[NH] = fmaf(oma, As, alpha * pre[NDTHR]);
       }
       loadD(yo + 1);
       // learned-estimator features of this output row: one warp per pixel
       if (a.feat != nullptr) {
-        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-        const int nbins = M * M * MZ;
-        for (int x = wid; x < TW; x += nw) {
+        constexpr int NDW = NDTHR / 32;
+        const int wid = dt >> 5;
+        constexpr int nbins = M * M * MZ;
+        for (int x = wid; x < TW; x += NDW) {
           if (x0 + x >= W) continue;
           const float* pb = pbuf + x * PS;
           float tot = 0.f;
@@ -416,35 +466,38 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
     };
 
     // ---- prologue: offsets, observer of row 0, x-DFT of row 0 ----------------
-    loadA(0);
+    if (owarp) loadA(0);
     // Per-plane offset removed from every Tw of this segment before the spatial
     // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
     // spatially constant offset per temporal plane (it only feeds the removed
     // kx = ky = 0 bin and the correction that cancels its window leakage), so
     // subtracting one constant per segment leaves the result unchanged while
     // keeping the FP32 sums at the scale of the texture instead of the DC level.
-    if (ua == 0) {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (owarp && ua == 0) {
+      cp_async_wait0();
+      float pa[MZ + 1];
       for (int f = 0; f <= MZ; ++f) pa[f] = abuf[f];
       float2 Tn[NPL], Tw0[NPL];
-      observer_hann<M, MZ>(pa, lam, hz, Tn, Tw0);
+      observer_hann<M, MZ>(pa, Tn, Tw0);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
     }
     loadD(y0);
     __syncthreads();
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    doA(0);
-    if (nrows > 1) loadA(1);
+    cp_async_wait0();
+    if (owarp) {
+      doA(0);
+      if (nrows > 1) loadA(1);
+    }
     __syncthreads();
     doB(0);
     __syncthreads();
 
-    // ---- pipelined rows: X = {y-SDFT(i), observer(i+1)}, Y = {reduce(i), x-DFT(i+1)}
+    // ---- pipelined rows: {y-SDFT(i), observer(i+1)}, {reduce(i), x-DFT(i+1)}
     for (int i = 0; i < nrows; ++i) {
       doC(i);
-      if (i + 1 < nrows) {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      if (owarp && i + 1 < nrows) {
+        cp_async_wait0();
         doA(i + 1);
         if (i + 2 < nrows) loadA(i + 2);
       }
@@ -453,39 +506,34 @@ __global__ void __launch_bounds__(kSpecMaxThreads, 2) spectrum_kernel(const Spec
       if (i + 1 < nrows) doB(i + 1);
       __syncthreads();
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    cp_async_wait0();
     __syncthreads();   // before the next segment rewrites offs
   }
 }
 
-}  // namespace
-
-// Shared-memory bytes and block size for a configuration (host side).
-struct SpecLaunch { int threads; size_t smem; };
-
-static SpecLaunch spec_launch_shape(int M, int Mz, int tw) {
-  return {spec_threads_for(M, Mz, tw), spec_smem_layout(M, Mz, tw).total};
-}
-
 template <int M, int MZ>
-static cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
-  SpecLaunch L = spec_launch_shape(M, MZ, a.tw);
-  auto kern = spectrum_kernel<M, MZ>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem));
+cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
+  using G = SG<M, MZ>;
+  if (a.tw != G::TW || a.kpad != G::KPAD) return cudaErrorInvalidValue;
+  const bool dump = a.dump_win != nullptr;
+  auto kern = dump ? spectrum_kernel<M, MZ, true> : spectrum_kernel<M, MZ, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM));
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.threads, L.smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NTHR, G::SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // one wave of CTAs, each with an equal share of the (strip, row) units
-  const long long units = (long long)((a.W + a.tw - 1) / a.tw) * a.H;
+  const long long units = (long long)((a.W + G::TW - 1) / G::TW) * a.H;
   long long grid = (long long)nsm * per_sm;
   if (grid > units) grid = units;
-  kern<<<unsigned(grid), L.threads, L.smem, st>>>(a);
+  kern<<<unsigned(grid), G::NTHR, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }
+
+}  // namespace
 
 #define WH_SPEC_CASES(X) \
   X(5, 3) X(5, 4) X(5, 5) X(5, 6) \
@@ -493,24 +541,41 @@ static cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   X(9, 3) X(9, 4) X(9, 5) X(9, 6) \
   X(15, 4) X(15, 5) X(15, 6)
 
-// Upload the constant twiddle tables for window M (all sizes at once, per device).
+// Upload the constant tables (all window sizes and temporal orders, per device).
 cudaError_t spectrum_init_constants() {
   static bool done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && done[dev]) return cudaSuccess;
+  const double pi = 3.14159265358979323846;
   float2 w[7][kMaxM], c[7][kMaxM];
   for (int mi = 0; mi < 7; ++mi) {
     const int M = 2 * mi + 3, K = (M - 1) / 2;
     for (int i = 0; i < kMaxM; ++i) {
       const int k = i - K;
-      const double pi = 3.14159265358979323846;
       w[mi][i] = make_float2(float(std::cos(2 * pi * k / M)), float(std::sin(2 * pi * k / M)));
       c[mi][i] = make_float2(float(std::cos(-2 * pi * k * K / M)), float(std::sin(-2 * pi * k * K / M)));
     }
   }
+  float2 lam[kZN][kMaxPlanes] = {}, hz[kZN] = {};
+  float cz[kZN][kMaxPlanes] = {}, sz[kZN][kMaxPlanes] = {};
+  for (int zi = 0; zi < kZN; ++zi) {
+    const int Mz = zi + 3;
+    for (int p = 0; p <= Mz / 2 && p < kMaxPlanes; ++p) {
+      // the Nyquist plane p = Mz/2 rotates by e^{j pi} = -1
+      lam[zi][p] = make_float2(float(std::cos(2 * pi * p / Mz)), float(std::sin(2 * pi * p / Mz)));
+      cz[zi][p] = float(std::cos(2 * pi * p / Mz));
+      sz[zi][p] = float(std::sin(2 * pi * p / Mz));
+    }
+    const double ph = -2 * pi * ((Mz - 1) / 2.0) / Mz;
+    hz[zi] = make_float2(float(std::cos(ph)), float(std::sin(ph)));
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_wres, w, sizeof(w));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cph, c, sizeof(c));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_lam, lam, sizeof(lam));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hz, hz, sizeof(hz));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cz, cz, sizeof(cz));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sz, sz, sizeof(sz));
   if (e == cudaSuccess && dev < 64) done[dev] = true;
   return e;
 }
@@ -522,8 +587,19 @@ bool spectrum_supported(int M, int Mz) {
   return false;
 }
 
-int spectrum_threads(int M, int Mz, int tw) { return spec_launch_shape(M, Mz, tw).threads; }
-size_t spectrum_smem(int M, int Mz, int tw) { return spec_launch_shape(M, Mz, tw).smem; }
+int spectrum_threads(int M, int Mz) {
+#define X(m, z) if (M == m && Mz == z) return SG<m, z>::NTHR;
+  WH_SPEC_CASES(X)
+#undef X
+  return 0;
+}
+
+size_t spectrum_smem(int M, int Mz) {
+#define X(m, z) if (M == m && Mz == z) return SG<m, z>::SMEM;
+  WH_SPEC_CASES(X)
+#undef X
+  return 0;
+}
 
 cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st) {
 #define X(m, z) if (a.M == m && a.Mz == z) return launch_spec_t<m, z>(a, st);

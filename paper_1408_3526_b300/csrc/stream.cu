@@ -23,8 +23,6 @@
 #include "tc_gemm.cuh"
 
 namespace wh {
-int spectrum_threads(int M, int Mz, int tw);
-size_t spectrum_smem(int M, int Mz, int tw);
 }  // namespace wh
 
 using namespace wh;
@@ -127,17 +125,6 @@ static void build_spec_tables(const wh_stream* s, SpecTables& tb, std::vector<in
   for (int ky = 1; ky <= K; ++ky) fill(hi++, 0, ky);
   for (int kx = 1; kx <= K; ++kx)
     for (int ky = -K; ky <= K; ++ky) fill(hi++, kx, ky);
-}
-
-static int pick_tile_w(int M, int Mz) {
-  const int K = (M - 1) / 2, J = (Mz - 1) / 2;
-  const bool even = (Mz % 2) == 0;
-  const int nchy = (1 + (even ? 1 : 0)) * (K + 1) + J * M;
-  // y-SDFT threads (rounded to warps) + one observer warp <= 384: two CTAs per SM
-  // and the row segment tw + 2K is covered by the observer warp's 32 lanes
-  int tw = 32 - 2 * K;
-  while (tw > 1 && ((tw * nchy + 31) / 32) * 32 + 32 > 384) --tw;
-  return tw;
 }
 
 // Learned mode: MLP velocity where its confidence passes the threshold (rounded
@@ -268,7 +255,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->L = L; s->precision = p.precision; s->debug = p.debug_dump;
   s->alpha = p.alpha; s->vmax = grid.vmax; s->vstep = grid.step;
   s->st = (cudaStream_t)cuda_stream;
-  s->tw = pick_tile_w(M, Mz);
+  s->tw = spec_tile_w(M, Mz);
   s->th = 64;
   s->kpad = ((M * M) + 3) & ~3;
   cudaGetDevice(&s->device);
@@ -397,12 +384,8 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
         return rc;
       }
   }
-  // the phase-D task split must fit the kernel's per-thread budget
-  const int nthr = spectrum_threads(M, Mz, s->tw);
-  const int nreal = 1 + (Mz % 2 == 0 ? 1 : 0), npl = (Mz - 1) / 2 + nreal;
-  const int nch_all = nreal * ((M - 1) / 2 + 1) + ((Mz - 1) / 2) * M + npl;
-  if (s->tw * ((M * M - 1) / 2 + 1) > 4 * nthr || s->tw * nch_all > 2 * nthr ||
-      spectrum_smem(M, Mz, s->tw) > 227 * 1024) {
+  // the spectrum kernel's shared memory must fit one CTA
+  if (spectrum_threads(M, Mz) <= 0 || spectrum_smem(M, Mz) > 227 * 1024) {
     free_stream(s);
     return WH_EUNSUP;
   }
