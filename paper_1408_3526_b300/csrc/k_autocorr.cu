@@ -16,7 +16,9 @@
 // Mapping: a warp works on two pixels, one per half-warp.  Stage 1: lane j
 // owns ly = +-l_j (twiddles for its ly in registers) and reads the pixel's
 // Q sums from shared memory by broadcast.  Stage 2: lane j owns lx = +-l_j
-// and reads T(., ly) by broadcast.
+// and reads T(., ly) by broadcast, two ly rows per 16-byte load.  The
+// (cos, sin) x (re, im) products run as packed FP32x2 FMAs, each component
+// rounded exactly as fmaf.
 #include "common.cuh"
 
 namespace wh {
@@ -41,17 +43,14 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   const int half = lane >> 4, j = lane & 15;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* qbuf = reinterpret_cast<float*>(smem_raw) + (wid * 2 + half) * QN;            // [QN]
+  const int Lp = (L + 1) & ~1;   // even row stride: rows (gy, gy+1) load as one float4
   float2* tbuf = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem_raw) + kWarps * 2 * QN) +
-                 (wid * 2 + half) * (K + 1) * L;                                        // [K+1][L]
-  // lane-owned twiddles: cos/sin(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
-  float cw[K], sw[K];
+                 (wid * 2 + half) * (K + 1) * Lp;                                       // [K+1][Lp]
+  // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
+  float2 cs[K];
   const bool act = j < Lh;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float2 e = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
-    cw[k] = e.x;
-    sw[k] = e.y;
-  }
+  for (int k = 0; k < K; ++k) cs[k] = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
   const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
   for (long long base = ((long long)blockIdx.x * kWarps + wid) * 2; base < npix;
        base += (long long)gridDim.x * kWarps * 2) {
@@ -99,17 +98,16 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
 #pragma unroll 2
       for (int kx = 0; kx <= K; ++kx) {
         const float2 z = q0[kx];
-        float va = z.x, vb = 0.f, vc = 0.f, vd = z.y;
+        float2 ac = make_float2(z.x, 0.f);   // (a, c)
+        float2 db = make_float2(z.y, 0.f);   // (d, b)
 #pragma unroll
         for (int ky = 0; ky < K; ++ky) {
           const float4 q = q4[kx * K + ky];
-          va = fmaf(q.x, cw[ky], va);
-          vb = fmaf(q.w, sw[ky], vb);
-          vc = fmaf(q.y, sw[ky], vc);
-          vd = fmaf(q.z, cw[ky], vd);
+          ac = __ffma2_rn(make_float2(q.x, q.y), cs[ky], ac);
+          db = __ffma2_rn(make_float2(q.z, q.w), cs[ky], db);
         }
-        tbuf[kx * L + gc + j] = make_float2(va - vb, vc + vd);
-        tbuf[kx * L + gc - j] = make_float2(va + vb, vd - vc);
+        tbuf[kx * Lp + gc + j] = make_float2(ac.x - db.y, ac.y + db.x);
+        tbuf[kx * Lp + gc - j] = make_float2(ac.x + db.y, db.x - ac.y);
       }
     }
     __syncwarp();
@@ -118,24 +116,36 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     int bidx = 0x7fffffff;
     if (valid && act) {
       const int gxp = gc + j, gxm = gc - j;
-      for (int gy = 0; gy < L; ++gy) {
-        float v1 = 0.f, v2 = 0.f;
-#pragma unroll
-        for (int kx = 1; kx <= K; ++kx) {
-          const float2 t = tbuf[kx * L + gy];
-          v1 = fmaf(cw[kx - 1], t.x, v1);
-          v2 = fmaf(sw[kx - 1], t.y, v2);
-        }
-        const float t0 = tbuf[gy].x;
-        const float rp = fmaf(2.f, v1 - v2, t0), rm = fmaf(2.f, v1 + v2, t0);
+      // candidates reach this lane in increasing flat index (im < ip, row by
+      // row), so keeping the first of equal values keeps the lowest index
+      auto take = [&](float r0, float2 v, int gy) {
+        const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
         const int ip = gy * L + gxp, im = gy * L + gxm;
         if (a.rs_out) {
           a.rs_out[pix * (L * L) + ip] = rp;
           if (j) a.rs_out[pix * (L * L) + im] = rm;
         }
-        // candidates in increasing flat index within this lane: im < ip
-        if (j && (rm > best || (rm == best && im < bidx))) { best = rm; bidx = im; }
-        if (rp > best || (rp == best && ip < bidx)) { best = rp; bidx = ip; }
+        if (rm > best) { best = rm; bidx = im; }
+        if (rp > best) { best = rp; bidx = ip; }
+      };
+      int gy = 0;
+      for (; gy + 1 < L; gy += 2) {
+        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int kx = 1; kx <= K; ++kx) {
+          const float4 t = *reinterpret_cast<const float4*>(tbuf + kx * Lp + gy);
+          v0 = __ffma2_rn(cs[kx - 1], make_float2(t.x, t.y), v0);
+          v1 = __ffma2_rn(cs[kx - 1], make_float2(t.z, t.w), v1);
+        }
+        const float4 t0 = *reinterpret_cast<const float4*>(tbuf + gy);
+        take(t0.x, v0, gy);
+        take(t0.z, v1, gy + 1);
+      }
+      if (gy < L) {
+        float2 v0 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int kx = 1; kx <= K; ++kx) v0 = __ffma2_rn(cs[kx - 1], tbuf[kx * Lp + gy], v0);
+        take(tbuf[gy].x, v0, gy);
       }
     }
 #pragma unroll
@@ -157,7 +167,7 @@ template <int M>
 cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
   constexpr int K = (M - 1) / 2;
   const size_t smem = sizeof(float) * size_t(kWarps) * 2 * AcSmem<M>::kQ +
-                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * a.L;
+                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * ((a.L + 1) & ~1);
   const long long npix = (long long)a.H * a.W;
   long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
   if (blocks > 148LL * 8) blocks = 148LL * 8;

@@ -19,10 +19,10 @@
 // Organisation: one CTA owns a strip of TW output columns and walks down its
 // share of rows one input row at a time (2K halo rows first); all geometry is
 // fixed at compile time by (M, Mz).  Per input row:
-//   A  (observer warp) observer update of the TW + 2K pixels of the row, Hann
-//      along kz, and the M-pixel box sums along x of every plane (warp
-//      shuffles) with their running sum over the last M rows, which is the
-//      removed (0,0) bin that the high-pass correction needs;
+//   A  (observer warp) observer update of the TW + 2K pixels of the row and
+//      Hann along kz; in the next phase the same warp forms the M-pixel box
+//      sums along x of every plane (warp shuffles) and their running sum over
+//      the last M rows, the removed (0,0) bin the high-pass correction needs;
 //   B  x-DFT units (x, kx >= 0, plane group): a direct M-tap sum with the
 //      Hann(x) window, the centring phase and the power scale folded into the
 //      weights; a complex plane's +kx and -kx outputs come from the same four
@@ -35,7 +35,7 @@
 //      offsets of the power block (+-h plus constants, no index table), the
 //      smoother update and the store; the next row's smoother state is
 //      prefetched with cp.async.
-// Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1)}.
+// Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1), box sums(i+1)}.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -48,12 +48,15 @@ namespace {
 
 constexpr int kZN = kMaxMz - 2;     // temporal orders Mz = 3 .. kMaxMz
 
-// Resonator twiddles e^{+j2pi ky/M} and centring phases e^{-j2pi ky K/M} per
-// window size (index (M-3)/2, ky+K); observer rotations, Hann(kz) phase and
-// the kz reduction's cos/sin per temporal order (index Mz-3).  Indexed at
-// compile time in the kernel, so they are read as constant-bank operands.
-__constant__ float2 c_wres[7][kMaxM];
-__constant__ float2 c_cph[7][kMaxM];
+// Resonator twiddles w_k = e^{+j2pi ky/M} and centring phases c_k =
+// e^{-j2pi ky K/M} (k = ky + K) per window size (index (M-3)/2), packed for
+// the bin pairs (p, p+K+1), p = 0..K-1: x, y and -y components of w (rw*) and
+// of c (rc*); the centre bin k = K has w = c = 1.  Observer rotations, Hann(kz)
+// phase and the kz reduction's cos/sin per temporal order (index Mz-3).  All
+// indexed at compile time in the kernel, so read as constant-bank operands.
+constexpr int kMaxK = (kMaxM - 1) / 2;
+__constant__ float2 c_rwx[7][kMaxK], c_rwy[7][kMaxK], c_rnwy[7][kMaxK];
+__constant__ float2 c_rcx[7][kMaxK], c_rcy[7][kMaxK], c_rncy[7][kMaxK];
 __constant__ float2 c_lam[kZN][kMaxPlanes];
 __constant__ float2 c_hz[kZN];
 __constant__ float c_cz[kZN][kMaxPlanes];
@@ -62,6 +65,33 @@ __constant__ float c_sz[kZN][kMaxPlanes];
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// Extra shared-memory wavefronts of the y-SDFT power stores (thread t writes
+// float (t % tw) * ps + (t / tw) * M + k) summed over the warps, for a pixel
+// stride ps of the power block.
+__host__ __device__ constexpr int pstore_conflicts(int tw, int nct, int M, int ps) {
+  int tot = 0;
+  for (int w0 = 0; w0 < nct; w0 += 32) {
+    int cnt[32] = {};
+    int mx = 0;
+    for (int t = w0; t < w0 + 32 && t < nct; ++t) {
+      const int b = ((t % tw) * ps + (t / tw) * M) % 32;
+      ++cnt[b];
+      if (cnt[b] > mx) mx = cnt[b];
+    }
+    tot += mx - 1;
+  }
+  return tot;
+}
+// Smallest conflict-free (else least-conflicting) stride >= the block size.
+__host__ __device__ constexpr int pick_pstride(int tw, int nct, int M, int minps) {
+  int best = minps, bc = 1 << 30;
+  for (int ps = minps; ps < minps + 32; ++ps) {
+    const int c = pstore_conflicts(tw, nct, M, ps);
+    if (c < bc) { bc = c; best = ps; }
+  }
+  return best;
+}
 
 // Compile-time geometry of one (M, Mz) configuration.
 template <int M, int MZ>
@@ -78,7 +108,7 @@ struct SG {
   static constexpr int RW = TW + 2 * K;
   static constexpr int NCT = TW * NCHY;                   // y-SDFT threads
   static constexpr int NTHR = cdiv(NCT, 32) * 32 + 32;    // + the observer warp
-  static constexpr int PS = (NCHY * M) | 1;               // odd pixel stride of pbuf
+  static constexpr int PS = pick_pstride(TW, NCT, M, NCHY * M);   // pixel stride of pbuf
   static constexpr int KPAD = (M * M + 3) & ~3;
   // x-DFT units (group, kx, x), group 0 = the real planes, j = complex plane j;
   // each group padded to whole warps so a warp runs one code path
@@ -87,13 +117,14 @@ struct SG {
   static constexpr int NBT = (J + 1) * GP;                // x-DFT threads
   static constexpr int NDT = TW * NH1;                    // reduction tasks per row
   // Reduction on the warps without x-DFT work, or on all warps, whichever has
-  // the shorter estimated critical path (x-DFT unit ~7 instr/tap, task ~28).
+  // the shorter estimated critical path (x-DFT unit ~7 instr/tap, task ~28);
+  // never on the observer warp, which runs the box sums meanwhile.
+  static constexpr int NTW = NTHR - 32;                   // threads other than the observer warp
   static constexpr int BCOST = 7 * M + 12, DCOST = 28;
-  static constexpr int SPLIT_COST =
-      (NBT < NTHR) ? imax(BCOST, cdiv(NDT, NTHR - NBT) * DCOST) : (1 << 30);
-  static constexpr int ALL_COST = BCOST + cdiv(NDT, NTHR) * DCOST;
+  static constexpr int SPLIT_COST = (NBT < NTW) ? imax(BCOST, cdiv(NDT, NTW - NBT) * DCOST) : (1 << 30);
+  static constexpr int ALL_COST = BCOST + cdiv(NDT, NTW) * DCOST;
   static constexpr int D0 = SPLIT_COST <= ALL_COST ? NBT : 0;   // first reduction thread
-  static constexpr int NDTHR = NTHR - D0;
+  static constexpr int NDTHR = NTW - D0;
   static constexpr int QD = cdiv(NDT, NDTHR);             // reduction rounds per row
   // first channel of plane p (channel order: plane 0 kx = 0..K, complex planes
   // kx = -K..K, Nyquist plane kx = 0..K)
@@ -110,7 +141,7 @@ struct SG {
   static constexpr size_t O_OFFS = al16(O_DPRE + 4ull * QD * 2 * NDTHR);       // float2 [NPL]
   static constexpr size_t SMEM = al16(O_OFFS + 8ull * NPL);
   static_assert(RW <= 32, "the observer warp covers the row segment");
-  static_assert(NBT <= NTHR, "one x-DFT unit per thread");
+  static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
 };
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
@@ -237,7 +268,7 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   const int ua = lane;
   const bool athr = owarp && ua < RW;
   // D: reduction thread index
-  const bool dthr = tid >= D0;
+  const bool dthr = tid >= D0 && tid < G::NTW;
   const int dt = tid - D0;
 
   // ---- this CTA's share of the (strip, row) units -------------------------------
@@ -255,9 +286,11 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     const int x0 = strip * TW;
     const int nrows = y1 - y0 + 2 * K;
 
-    float2 Y[M];
+    // y-resonator state: bins (p, p+K+1) packed as (re, re) and (im, im) pairs,
+    // and the centre bin K
+    float2 YR[K], YI[K], Yc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < M; ++k) Y[k] = make_float2(0.f, 0.f);
+    for (int p = 0; p < K; ++p) { YR[p] = make_float2(0.f, 0.f); YI[p] = make_float2(0.f, 0.f); }
 
     auto loadA = [&](int i) {             // prefetch input row i into this lane's abuf slot
       if (athr) {
@@ -270,43 +303,39 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       }
       cp_async_commit();
     };
-    auto doA = [&](int i) {               // whole observer warp: observer, Hann(kz), box sums
+    auto doA = [&](int i) {               // observer update + Hann(kz) of input row i
+      if (!athr) return;
       const int r = y0 - K + i;
-      float2 v[NPL];
-      if (athr) {
-        float pa[MZ + 1];
+      float pa[MZ + 1];
 #pragma unroll
-        for (int f = 0; f <= MZ; ++f) pa[f] = abuf[ua * (MZ + 1) + f];
-        float2 T[NPL], Tw[NPL];
-        observer_hann<M, MZ>(pa, T, Tw);
-        const int xs = x0 - K + ua;
-        if (r >= y0 && r < y1 && ua >= K && ua < K + TW && xs < W) {   // owner writes the new state
-          const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
-          a.obs_new[o] = T[0].x;
+      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[ua * (MZ + 1) + f];
+      float2 T[NPL], Tw[NPL];
+      observer_hann<M, MZ>(pa, T, Tw);
+      const int xs = x0 - K + ua;
+      if (r >= y0 && r < y1 && ua >= K && ua < K + TW && xs < W) {   // owner writes the new state
+        const size_t o = size_t(r) * W + xs, plane = size_t(H) * W;
+        a.obs_new[o] = T[0].x;
 #pragma unroll
-          for (int j = 1; j <= J; ++j) {
-            a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
-            a.obs_new[(2 * j) * plane + o] = T[j].y;
-          }
-          if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
+        for (int j = 1; j <= J; ++j) {
+          a.obs_new[(2 * j - 1) * plane + o] = T[j].x;
+          a.obs_new[(2 * j) * plane + o] = T[j].y;
         }
-#pragma unroll
-        for (int p = 0; p < NPL; ++p) {
-          v[p] = csub(Tw[p], offs[p]);
-          twr[p * RW + ua] = v[p];
-        }
-      } else {
-#pragma unroll
-        for (int p = 0; p < NPL; ++p) v[p] = make_float2(0.f, 0.f);
+        if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
       }
-      // box sums along x (the (0,0) bin of the row window at column ua), their
-      // running sum over the last M rows, and a ring of the last M+1 rows' sums
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) twr[p * RW + ua] = csub(Tw[p], offs[p]);
+    };
+    // whole observer warp: box sums along x of input row i (the (0,0) bin of
+    // the row window at column ua), their running sum over the last M rows and
+    // a ring of the last M+1 rows' sums
+    auto doA2 = [&](int i) {
       float2 bs[NPL];
 #pragma unroll
       for (int p = 0; p < NPL; ++p) {
         const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        bs[p].x = lane_box_sum<M>(v[p].x);
-        bs[p].y = real ? 0.f : lane_box_sum<M>(v[p].y);
+        const float2 v = ua < RW ? twr[p * RW + ua] : make_float2(0.f, 0.f);
+        bs[p].x = lane_box_sum<M>(v.x);
+        bs[p].y = real ? 0.f : lane_box_sum<M>(v.y);
       }
       if (ua < TW) {
         const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);   // oslot holds row i - M
@@ -383,38 +412,63 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       const float2 xn = ring[(i % (M + 1)) * RING_SLOT + tid];
       float2 d = xn;
       if (i >= M) d = csub(xn, ring[((i + 1) % (M + 1)) * RING_SLOT + tid]);
+      // Y_k <- w_k Y_k + c_k d for the bin pairs (packed), and the centre bin
+      // (w = c = 1); per component the same fmaf sequence as the complex form
+      const float2 dx2 = make_float2(d.x, d.x), dy2 = make_float2(d.y, d.y);
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const float2 w = c_wres[MI][k], c = c_cph[MI][k];
-        Y[k] = make_float2(fmaf(w.x, Y[k].x, fmaf(-w.y, Y[k].y, fmaf(c.x, d.x, -c.y * d.y))),
-                           fmaf(w.x, Y[k].y, fmaf(w.y, Y[k].x, fmaf(c.x, d.y, c.y * d.x))));
+      for (int p = 0; p < K; ++p) {
+        const float2 tr = __ffma2_rn(c_rcx[MI][p], dx2, __fmul2_rn(c_rncy[MI][p], dy2));
+        const float2 ti = __ffma2_rn(c_rcx[MI][p], dy2, __fmul2_rn(c_rcy[MI][p], dx2));
+        const float2 r = YR[p];
+        YR[p] = __ffma2_rn(c_rwx[MI][p], r, __ffma2_rn(c_rnwy[MI][p], YI[p], tr));
+        YI[p] = __ffma2_rn(c_rwx[MI][p], YI[p], __ffma2_rn(c_rwy[MI][p], r, ti));
       }
+      Yc = cadd(Yc, d);
       if (!(i >= 2 * K && yo < y1)) return;
       // 4 x [Hann along ky (taps 1/4, 1/2, 1/4 in the centred basis), minus
       // Hann_x Hann_y of the removed (0,0) bin]; the 1/16 is in sig^2
       const float2 D = dbuf[(i & 1) * DC_SLOT + plc * TW + xy];
       float* pb = pbuf + xy * PS + cy * M;
+      const float2 two2 = make_float2(2.f, 2.f);
+      auto dump = [&](int k, float zx, float zy, float pw) {
+        // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
+        if (!(DUMP && x0 + xy < W)) return;
+        const SpecTables& tb = *a.tables;
+        const size_t pix = size_t(yo) * W + x0 + xy;
+        const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
+        const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), make_float2(zx, zy)),
+                                 0.25f * float(MZ) / sqrtf(float(M * M * MZ)) / sig);
+        const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
+        const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
+        a.dump_win[op] = sv;
+        a.dump_win[om] = conjf2(sv);
+        if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
+      };
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        float2 z = cadd(cscale(Y[k], 2.f), cadd(Y[(k + 1) % M], Y[(k + M - 1) % M]));
-        if (k == K) z = csub(z, cscale(D, wxh * 2.f));
-        if (k == K - 1 || k == K + 1) z = csub(z, cscale(D, wxh));
-        const float pw = fmaf(z.x, z.x, z.y * z.y);
-        pb[k] = pw;
-        if (DUMP && x0 + xy < W) {
-          // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
-          const SpecTables& tb = *a.tables;
-          const size_t pix = size_t(yo) * W + x0 + xy;
-          const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
-          const float2 sv = cscale(cmul(cmul(tb.uncenter[kxc + K], tb.uncenter[k]), z),
-                                   0.25f * float(MZ) / sqrtf(float(M * M * MZ)) / sig);
-          const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
-          const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
-          a.dump_win[op] = sv;
-          a.dump_win[om] = conjf2(sv);
-          if (a.dump_pow) { a.dump_pow[op] = pw; a.dump_pow[om] = pw; }
-        }
+      for (int p = 0; p < K; ++p) {
+        // neighbours k+1 and k-1 of the pair's bins (k = p, p+K+1), cyclic in k
+        float2 nr, ni, mr, mi;
+        if (p + 1 < K) { nr = YR[p + 1]; ni = YI[p + 1]; }
+        else { nr = make_float2(Yc.x, YR[0].x); ni = make_float2(Yc.y, YI[0].x); }
+        if (p > 0) { mr = YR[p - 1]; mi = YI[p - 1]; }
+        else { mr = make_float2(YR[K - 1].y, Yc.x); mi = make_float2(YI[K - 1].y, Yc.y); }
+        float2 zr = __ffma2_rn(two2, YR[p], __fadd2_rn(nr, mr));
+        float2 zi = __ffma2_rn(two2, YI[p], __fadd2_rn(ni, mi));
+        if (p == K - 1) { zr.x -= D.x * wxh; zi.x -= D.y * wxh; }   // bin K-1
+        if (p == 0) { zr.y -= D.x * wxh; zi.y -= D.y * wxh; }       // bin K+1
+        const float2 pw = __ffma2_rn(zr, zr, __fmul2_rn(zi, zi));
+        pb[p] = pw.x;
+        pb[p + K + 1] = pw.y;
+        dump(p, zr.x, zi.x, pw.x);
+        dump(p + K + 1, zr.y, zi.y, pw.y);
       }
+      // centre bin K
+      float zcx = fmaf(2.f, Yc.x, YR[0].y + YR[K - 1].x), zcy = fmaf(2.f, Yc.y, YI[0].y + YI[K - 1].x);
+      zcx -= D.x * (wxh * 2.f);
+      zcy -= D.y * (wxh * 2.f);
+      const float pwc = fmaf(zcx, zcx, zcy * zcy);
+      pb[K] = pwc;
+      dump(K, zcx, zcy, pwc);
     };
     auto doD = [&](int i) {               // reduce over kz, smooth, store (output row of i)
       const int yo = y0 + i - 2 * K;
@@ -491,9 +545,11 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     }
     __syncthreads();
     doB(0);
+    if (owarp) doA2(0);
     __syncthreads();
 
-    // ---- pipelined rows: {y-SDFT(i), observer(i+1)}, {reduce(i), x-DFT(i+1)}
+    // ---- pipelined rows: {y-SDFT(i), observer(i+1)},
+    //      {reduce(i), x-DFT(i+1), box sums(i+1)}
     for (int i = 0; i < nrows; ++i) {
       doC(i);
       if (owarp && i + 1 < nrows) {
@@ -503,7 +559,10 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       }
       __syncthreads();
       doD(i);
-      if (i + 1 < nrows) doB(i + 1);
+      if (i + 1 < nrows) {
+        doB(i + 1);
+        if (owarp) doA2(i + 1);
+      }
       __syncthreads();
     }
     cp_async_wait0();
@@ -570,8 +629,26 @@ cudaError_t spectrum_init_constants() {
     const double ph = -2 * pi * ((Mz - 1) / 2.0) / Mz;
     hz[zi] = make_float2(float(std::cos(ph)), float(std::sin(ph)));
   }
-  cudaError_t e = cudaMemcpyToSymbol(c_wres, w, sizeof(w));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cph, c, sizeof(c));
+  float2 rwx[7][kMaxK] = {}, rwy[7][kMaxK] = {}, rnwy[7][kMaxK] = {};
+  float2 rcx[7][kMaxK] = {}, rcy[7][kMaxK] = {}, rncy[7][kMaxK] = {};
+  for (int mi = 0; mi < 7; ++mi) {
+    const int K = mi + 1;
+    for (int p = 0; p < K; ++p) {
+      const int q = p + K + 1;
+      rwx[mi][p] = make_float2(w[mi][p].x, w[mi][q].x);
+      rwy[mi][p] = make_float2(w[mi][p].y, w[mi][q].y);
+      rnwy[mi][p] = make_float2(-w[mi][p].y, -w[mi][q].y);
+      rcx[mi][p] = make_float2(c[mi][p].x, c[mi][q].x);
+      rcy[mi][p] = make_float2(c[mi][p].y, c[mi][q].y);
+      rncy[mi][p] = make_float2(-c[mi][p].y, -c[mi][q].y);
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_rwx, rwx, sizeof(rwx));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rwy, rwy, sizeof(rwy));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rnwy, rnwy, sizeof(rnwy));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcx, rcx, sizeof(rcx));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcy, rcy, sizeof(rcy));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rncy, rncy, sizeof(rncy));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_lam, lam, sizeof(lam));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hz, hz, sizeof(hz));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cz, cz, sizeof(cz));
