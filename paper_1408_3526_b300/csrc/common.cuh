@@ -102,9 +102,23 @@ struct PefArgs {
   int H, W, M, Mz, L, mpz;
   const float* obs;             // T_t, just written
   const int* vidx;
-  const float* hw;              // [L][Mz][M] separable FIR weights (Eq. (2)), incl. scale
+  // separable FIR weights h(d; v, mz) of Eq. (2), incl. scale, in one buffer
+  // (layout: pef_hw2_offset / pef_hwp_offset):
+  //   float  [L][Mz][M]            h
+  //   float2 [L][Mz][M]            (h, h)              at pef_hw2_offset floats
+  //   float2 [L][Mz][(M-1)/2]      (h(2i), h(2i+1))    at pef_hwp_offset floats
+  const float* hw;
   float* whitened;
 };
+__host__ __device__ inline size_t pef_hw2_offset(int L, int Mz, int M) {
+  return (size_t(L) * Mz * M + 3) & ~size_t(3);
+}
+__host__ __device__ inline size_t pef_hwp_offset(int L, int Mz, int M) {
+  return pef_hw2_offset(L, Mz, M) + 2 * size_t(L) * Mz * M;
+}
+__host__ __device__ inline size_t pef_table_floats(int L, int Mz, int M) {
+  return pef_hwp_offset(L, Mz, M) + 2 * size_t(L) * Mz * ((M - 1) / 2);
+}
 
 struct RawSpecArgs {
   int H, W, M, Mz;

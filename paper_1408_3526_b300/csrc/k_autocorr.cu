@@ -32,33 +32,57 @@ struct AcSmem {
   static constexpr int K = (M - 1) / 2;
   // per pixel: Q sums [K+1][K] x 4 (sr, dr, si, di) + Q(kx,0) [K+1] x 2
   static constexpr int kQ = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;   // 16-byte multiple
+  static constexpr int kPad = (M * M + 3) & ~3;                          // state row (floats)
 };
 
-template <int M>
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int M, bool RS>
 __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArgs a) {
   constexpr int K = (M - 1) / 2;
-  constexpr int QN = AcSmem<M>::kQ;
+  constexpr int QN = AcSmem<M>::kQ, KP = AcSmem<M>::kPad;
   const int L = a.L, Lh = (L + 1) / 2, gc = (L - 1) / 2, nh = (M * M - 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int half = lane >> 4, j = lane & 15;
+  const int hw = wid * 2 + half;                        // half-warp (pixel slot) in the block
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* qbuf = reinterpret_cast<float*>(smem_raw) + (wid * 2 + half) * QN;            // [QN]
+  float* sbase = reinterpret_cast<float*>(smem_raw);
+  float* abuf = sbase + hw * 2 * KP;                                                    // [2][KP]
+  float* qbuf = sbase + kWarps * 2 * 2 * KP + hw * QN;                                  // [QN]
   const int Lp = (L + 1) & ~1;   // even row stride: rows (gy, gy+1) load as one float4
-  float2* tbuf = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem_raw) + kWarps * 2 * QN) +
-                 (wid * 2 + half) * (K + 1) * Lp;                                       // [K+1][Lp]
+  float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * (K + 1) * Lp;   // [K+1][Lp]
   // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
   float2 cs[K];
   const bool act = j < Lh;
 #pragma unroll
   for (int k = 0; k < K; ++k) cs[k] = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
   const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
-  for (long long base = ((long long)blockIdx.x * kWarps + wid) * 2; base < npix;
-       base += (long long)gridDim.x * kWarps * 2) {
+  const long long stride = (long long)gridDim.x * kWarps * 2;
+  auto pixel_of = [&](long long b) -> long long {
+    return a.pix_list ? (long long)a.pix_list[b] : b;
+  };
+  // the state row of this half-warp's pixel at b -> abuf slot (16-byte copies)
+  auto prefetch = [&](long long b, int slot) {
+    if (b < npix) {
+      const float* src = a.Astate + pixel_of(b) * KP;
+      for (int c = j; c < KP / 4; c += kHalf) cp_async16(abuf + slot * KP + 4 * c, src + 4 * c);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  long long base = ((long long)blockIdx.x * kWarps + wid) * 2;
+  prefetch(base + half, 0);
+  for (int it = 0; base < npix; base += stride, ++it) {
     const bool valid = base + half < npix;
-    const long long pix = !valid ? 0 : (a.pix_list ? (long long)a.pix_list[base + half] : base + half);
+    const long long pix = valid ? pixel_of(base + half) : 0;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    prefetch(base + stride + half, (it + 1) & 1);
     // ---- Q sums of this half-warp's pixel ----------------------------------
     if (valid) {
-      const float* A = a.Astate + pix * a.kpad;
+      const float* A = abuf + (it & 1) * KP;
       for (int e = j; e < (K + 1) * K; e += kHalf) {
         const int kx = e / K, ky = e % K + 1;
         float sr, dr, si, di;
@@ -72,10 +96,7 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
           const float rp = A[hp], rm = A[hm], ip = A[nh + hp], im = A[nh + hm];
           sr = rp + rm; dr = rp - rm; si = ip + im; di = ip - im;
         }
-        qbuf[4 * e + 0] = sr;
-        qbuf[4 * e + 1] = dr;
-        qbuf[4 * e + 2] = si;
-        qbuf[4 * e + 3] = di;
+        reinterpret_cast<float4*>(qbuf)[e] = make_float4(sr, dr, si, di);
       }
       if (j <= K) {
         const int kx = j;
@@ -86,8 +107,7 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
           qr = A[h0];
           qi = A[nh + h0];
         }
-        qbuf[4 * (K + 1) * K + 2 * kx] = qr;
-        qbuf[4 * (K + 1) * K + 2 * kx + 1] = qi;
+        reinterpret_cast<float2*>(qbuf + 4 * (K + 1) * K)[kx] = make_float2(qr, qi);
       }
     }
     __syncwarp();
@@ -112,21 +132,27 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     }
     __syncwarp();
     // ---- stage 2: R(+-lx_j, ly) and argmax ------------------------------------
+    // R(+lx) = t0 + 2(v1 - v2), R(-lx) = t0 + 2(v1 + v2); their larger one is
+    // exactly t0 + 2(v1 + |v2|) (the same rounded operations).  Candidates reach
+    // this lane in increasing flat index (R(-lx) before R(+lx), row by row), so
+    // the first row reaching the maximum is kept and resolved at the end.
     float best = -INFINITY;
     int bidx = 0x7fffffff;
     if (valid && act) {
-      const int gxp = gc + j, gxm = gc - j;
-      // candidates reach this lane in increasing flat index (im < ip, row by
-      // row), so keeping the first of equal values keeps the lowest index
+      int bgy = 0;
+      auto row_v = [&](int gy) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int kx = 1; kx <= K; ++kx) v = __ffma2_rn(cs[kx - 1], tbuf[kx * Lp + gy], v);
+        return v;
+      };
       auto take = [&](float r0, float2 v, int gy) {
-        const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
-        const int ip = gy * L + gxp, im = gy * L + gxm;
-        if (a.rs_out) {
-          a.rs_out[pix * (L * L) + ip] = rp;
-          if (j) a.rs_out[pix * (L * L) + im] = rm;
+        if (RS) {
+          a.rs_out[pix * (L * L) + gy * L + gc + j] = fmaf(2.f, v.x - v.y, r0);
+          if (j) a.rs_out[pix * (L * L) + gy * L + gc - j] = fmaf(2.f, v.x + v.y, r0);
         }
-        if (rm > best) { best = rm; bidx = im; }
-        if (rp > best) { best = rp; bidx = ip; }
+        const float m = fmaf(2.f, v.x + fabsf(v.y), r0);
+        if (m > best) { best = m; bgy = gy; }
       };
       int gy = 0;
       for (; gy + 1 < L; gy += 2) {
@@ -141,12 +167,12 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
         take(t0.x, v0, gy);
         take(t0.z, v1, gy + 1);
       }
-      if (gy < L) {
-        float2 v0 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int kx = 1; kx <= K; ++kx) v0 = __ffma2_rn(cs[kx - 1], tbuf[kx * Lp + gy], v0);
-        take(tbuf[gy].x, v0, gy);
-      }
+      if (gy < L) take(tbuf[gy].x, row_v(gy), gy);
+      // which of R(-lx), R(+lx) of the best row holds the maximum (-lx first)
+      const float2 v = row_v(bgy);
+      const float r0 = tbuf[bgy].x;
+      const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
+      bidx = bgy * L + (rm >= rp ? gc - j : gc + j);
     }
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) {
@@ -161,20 +187,22 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     }
     __syncwarp();
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <int M>
 cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
   constexpr int K = (M - 1) / 2;
-  const size_t smem = sizeof(float) * size_t(kWarps) * 2 * AcSmem<M>::kQ +
+  if (a.kpad != AcSmem<M>::kPad) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * size_t(kWarps) * 2 * (2 * AcSmem<M>::kPad + AcSmem<M>::kQ) +
                       sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * ((a.L + 1) & ~1);
   const long long npix = (long long)a.H * a.W;
   long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
   if (blocks > 148LL * 8) blocks = 148LL * 8;
-  cudaError_t e = cudaFuncSetAttribute(autocorr_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem));
+  auto kern = a.rs_out ? autocorr_kernel<M, true> : autocorr_kernel<M, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  autocorr_kernel<M><<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
+  kern<<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -24,23 +24,32 @@ namespace {
 
 constexpr int kT = 16;
 
+template <int M>
+struct PefGeo {
+  static constexpr int K = (M - 1) / 2;
+  static constexpr int RT = kT + 2 * K;   // history tile edge
+};
+
+// One CTA per 16 x 16 output tile.  The history tile is kept as pairs of
+// consecutive rows, hp[m][r][x] = (x(r), x(r+1)), so one 8-byte load feeds a
+// packed FP32x2 FMA over the taps dy = 2i, 2i+1 of the y-sum; the x-weights of
+// the pixel's velocity come duplicated, (h, h), from the L1-cached table.
+template <int M, int MZ>
 __global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
-  const int M = a.M, K = (M - 1) / 2, Mz = a.Mz, L = a.L, H = a.H, W = a.W;
-  const int J = (Mz - 1) / 2;
-  const bool even = (Mz % 2) == 0;
-  const int RT = kT + 2 * K;
+  constexpr int K = PefGeo<M>::K, RT = PefGeo<M>::RT;
+  constexpr int J = (MZ - 1) / 2;
+  constexpr bool EVEN = (MZ % 2) == 0;
+  const int L = a.L, H = a.H, W = a.W;
   const int x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* hist = reinterpret_cast<float*>(smem_raw);      // [Mz][RT][RT]
-  float* hw = hist + Mz * RT * RT;                         // [L][Mz][M]
-  float* cs = hw + L * Mz * M;                             // [J+1][Mz] cos, then sin
-  float* sn = cs + (J + 1) * Mz;
+  float2* hp = reinterpret_cast<float2*>(smem_raw);        // [MZ][RT][RT]
+  float* cs = reinterpret_cast<float*>(hp + MZ * RT * RT);  // [J+1][MZ] cos, then sin
+  float* sn = cs + (J + 1) * MZ;
   const int tid = threadIdx.y * kT + threadIdx.x, nthr = kT * kT;
-  for (int i = tid; i < L * Mz * M; i += nthr) hw[i] = a.hw[i];
-  for (int i = tid; i < (J + 1) * Mz; i += nthr) {
-    const int j = i / Mz, m = i % Mz;
+  for (int i = tid; i < (J + 1) * MZ; i += nthr) {
+    const int j = i / MZ, m = i % MZ;
     float s, c;
-    sincospif(2.0f * float((j * m) % Mz) / float(Mz), &s, &c);
+    sincospif(2.0f * float((j * m) % MZ) / float(MZ), &s, &c);
     cs[i] = c;
     sn[i] = s;
   }
@@ -52,14 +61,20 @@ __global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
     ys = ys < 0 ? 0 : (ys >= H ? H - 1 : ys);
     xs = xs < 0 ? 0 : (xs >= W ? W - 1 : xs);
     const size_t o = size_t(ys) * W + xs;
-    float st[kMaxMz];
-    for (int f = 0; f < Mz; ++f) st[f] = __ldg(a.obs + f * plane + o);
-    for (int m = 0; m < Mz; ++m) {
+    float st[MZ];
+#pragma unroll
+    for (int f = 0; f < MZ; ++f) st[f] = __ldg(a.obs + f * plane + o);
+#pragma unroll
+    for (int m = 0; m < MZ; ++m) {
       float v = st[0];
+#pragma unroll
       for (int j = 1; j <= J; ++j)
-        v += 2.f * (st[2 * j - 1] * cs[j * Mz + m] + st[2 * j] * sn[j * Mz + m]);
-      if (even) v += (m & 1) ? -st[Mz - 1] : st[Mz - 1];
-      hist[(m * RT + yy) * RT + xx] = v;
+        v += 2.f * (st[2 * j - 1] * cs[j * MZ + m] + st[2 * j] * sn[j * MZ + m]);
+      if (EVEN) v += (m & 1) ? -st[MZ - 1] : st[MZ - 1];
+      float2* row = hp + (m * RT + yy) * RT + xx;
+      row->x = v;
+      if (yy > 0) row[-RT].y = v;
+      if (yy == RT - 1) row->y = 0.f;
     }
   }
   __syncthreads();
@@ -69,21 +84,30 @@ __global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
   const size_t pix = size_t(py) * W + px;
   const int g = a.vidx[pix];
   const int gx = g % L, gy = g / L;
+  const float2* hw2 = reinterpret_cast<const float2*>(a.hw + pef_hw2_offset(L, MZ, M)) + size_t(gx) * MZ * M;
+  const float2* hwp = reinterpret_cast<const float2*>(a.hw + pef_hwp_offset(L, MZ, M)) + size_t(gy) * MZ * K;
+  const float* hwy = a.hw + size_t(gy) * MZ * M;
   float Ihat = 0.f;
-  for (int m = 0; m < Mz; ++m) {
-    const float* hxr = hw + (gx * Mz + m) * M;
-    const float* hyr = hw + (gy * Mz + m) * M;
-    const float* hb = hist + (m * RT + ty) * RT + tx;
-    float acc = 0.f;
-    for (int dy = 0; dy < M; ++dy) {
-      const float* row = hb + dy * RT;
-      float r = 0.f;
-      for (int dx = 0; dx < M; ++dx) r = fmaf(hxr[dx], row[dx], r);
-      acc = fmaf(hyr[dy], r, acc);
+#pragma unroll
+  for (int m = 0; m < MZ; ++m) {
+    float2 wx[M];
+#pragma unroll
+    for (int dx = 0; dx < M; ++dx) wx[dx] = __ldg(hw2 + m * M + dx);
+    const float2* hb = hp + (m * RT + ty) * RT + tx;
+    float2 acc = make_float2(0.f, 0.f);              // (even dy, odd dy) partial sums
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float2 r = make_float2(0.f, 0.f);              // x-sums of rows dy = 2i, 2i+1
+#pragma unroll
+      for (int dx = 0; dx < M; ++dx) r = __ffma2_rn(wx[dx], hb[(2 * i) * RT + dx], r);
+      acc = __ffma2_rn(__ldg(hwp + m * K + i), r, acc);
     }
-    Ihat += acc;
+    float rl = 0.f;                                   // last row dy = 2K
+#pragma unroll
+    for (int dx = 0; dx < M; ++dx) rl = fmaf(wx[dx].x, hb[(2 * K) * RT + dx].x, rl);
+    Ihat += fmaf(__ldg(hwy + m * M + 2 * K), rl, acc.x + acc.y);
   }
-  a.whitened[pix] = hist[(a.mpz * RT + ty + K) * RT + tx + K] - Ihat;
+  a.whitened[pix] = hp[(a.mpz * RT + ty + K) * RT + tx + K].x - Ihat;
 }
 
 // Raw spectrum S(k; n) of Eq. (6)-(7) from the observer state, by direct
@@ -127,15 +151,28 @@ __global__ void raw_spectrum_kernel(const RawSpecArgs a) {
 
 }  // namespace
 
-cudaError_t launch_pef(const PefArgs& a, cudaStream_t st) {
-  const int K = (a.M - 1) / 2, RT = kT + 2 * K, J = (a.Mz - 1) / 2;
-  const size_t smem = sizeof(float) * (size_t(a.Mz) * RT * RT + size_t(a.L) * a.Mz * a.M +
-                                       2 * size_t(J + 1) * a.Mz);
-  cudaError_t e = cudaFuncSetAttribute(pef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+template <int M, int MZ>
+static cudaError_t launch_pef_t(const PefArgs& a, cudaStream_t st) {
+  constexpr int RT = PefGeo<M>::RT, J = (MZ - 1) / 2;
+  const size_t smem = sizeof(float2) * size_t(MZ) * RT * RT + sizeof(float) * 2 * size_t(J + 1) * MZ;
+  cudaError_t e = cudaFuncSetAttribute(pef_kernel<M, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   dim3 grid((a.W + kT - 1) / kT, (a.H + kT - 1) / kT);
-  pef_kernel<<<grid, dim3(kT, kT), smem, st>>>(a);
+  pef_kernel<M, MZ><<<grid, dim3(kT, kT), smem, st>>>(a);
   return cudaGetLastError();
+}
+
+#define WH_PEF_CASES(X) \
+  X(5, 3) X(5, 4) X(5, 5) X(5, 6) \
+  X(7, 3) X(7, 4) X(7, 5) X(7, 6) \
+  X(9, 3) X(9, 4) X(9, 5) X(9, 6) \
+  X(15, 4) X(15, 5) X(15, 6)
+
+cudaError_t launch_pef(const PefArgs& a, cudaStream_t st) {
+#define X(m, z) if (a.M == m && a.Mz == z) return launch_pef_t<m, z>(a, st);
+  WH_PEF_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st) {

@@ -301,14 +301,25 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   }
   const int Wb = 2 * s->B + 1;
   const double hscale = std::sqrt(double(Wb) * Wb / (double(M) * M * Mz));
-  std::vector<float> hw(size_t(L) * Mz * M);
+  std::vector<float> hw(pef_table_floats(L, Mz, M), 0.f);
+  float* hw2 = hw.data() + pef_hw2_offset(L, Mz, M);
+  float* hwp = hw.data() + pef_hwp_offset(L, Mz, M);
   for (int g = 0; g < L; ++g) {
     const double v = -s->vmax + g * s->vstep;
-    for (int m = 0; m < Mz; ++m)
+    for (int m = 0; m < Mz; ++m) {
+      const size_t r = size_t(g) * Mz + m;
       for (int j = 0; j < M; ++j) {
         const int d = j - K;
-        hw[(size_t(g) * Mz + m) * M + j] = float(hscale * dirichlet(Wb, (d + v * (m - s->mpz)) / M));
+        const float h = float(hscale * dirichlet(Wb, (d + v * (m - s->mpz)) / M));
+        hw[r * M + j] = h;
+        hw2[2 * (r * M + j)] = h;
+        hw2[2 * (r * M + j) + 1] = h;
       }
+      for (int i = 0; i < K; ++i) {
+        hwp[2 * (r * K + i)] = hw[r * M + 2 * i];
+        hwp[2 * (r * K + i) + 1] = hw[r * M + 2 * i + 1];
+      }
+    }
   }
   alloc((void**)&s->d_hgather, sizeof(int) * hg.size());
   alloc((void**)&s->d_taby, sizeof(float2) * taby.size());
