@@ -52,13 +52,28 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   float* sbase = reinterpret_cast<float*>(smem_raw);
   float* abuf = sbase + hw * 2 * KP;                                                    // [2][KP]
   float* qbuf = sbase + kWarps * 2 * 2 * KP + hw * QN;                                  // [QN]
-  const int Lp = (L + 1) & ~1;   // even row stride: rows (gy, gy+1) load as one float4
+  constexpr int Lp = 2 * kHalf;   // row stride (>= L, even: rows gy, gy+1 load as one float4)
   float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * (K + 1) * Lp;   // [K+1][Lp]
   // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
   float2 cs[K];
   const bool act = j < Lh;
 #pragma unroll
   for (int k = 0; k < K; ++k) cs[k] = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
+  // Q-sum elements e = j + 16 r of this lane: offsets hp, hm of A(kx, +ky) and
+  // A(kx, -ky) in the half-plane state, and a sign bit that conjugates the
+  // second one for kx = 0 (A(0, -ky) = conj A(0, ky) is stored as A(0, ky))
+  constexpr int NE = (K + 1) * K, QIT = (NE + kHalf - 1) / kHalf;
+  int qoff[QIT];
+#pragma unroll
+  for (int r = 0; r < QIT; ++r) {
+    const int e = j + kHalf * r;
+    const int kx = e / K, ky = e % K + 1;
+    int hp, hm, neg;
+    if (kx == 0) { hp = ky; hm = ky; neg = 1; }
+    else { hp = K + (kx - 1) * M + (ky + K) + 1; hm = K + (kx - 1) * M + (-ky + K) + 1; neg = 0; }
+    qoff[r] = e < NE ? (hp | (hm << 8) | (neg << 16)) : -1;
+  }
+  const float invL = 1.0f / float(L);
   const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
   const long long stride = (long long)gridDim.x * kWarps * 2;
   auto pixel_of = [&](long long b) -> long long {
@@ -83,31 +98,19 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     // ---- Q sums of this half-warp's pixel ----------------------------------
     if (valid) {
       const float* A = abuf + (it & 1) * KP;
-      for (int e = j; e < (K + 1) * K; e += kHalf) {
-        const int kx = e / K, ky = e % K + 1;
-        float sr, dr, si, di;
-        if (kx == 0) {
-          sr = 2.f * A[ky];
-          dr = 0.f;
-          si = 0.f;
-          di = 2.f * A[nh + ky];
-        } else {
-          const int hp = K + (kx - 1) * M + (ky + K) + 1, hm = K + (kx - 1) * M + (-ky + K) + 1;
-          const float rp = A[hp], rm = A[hm], ip = A[nh + hp], im = A[nh + hm];
-          sr = rp + rm; dr = rp - rm; si = ip + im; di = ip - im;
+#pragma unroll
+      for (int r = 0; r < QIT; ++r) {
+        const int t = qoff[r];
+        if (t >= 0) {
+          const int hp = t & 0xff, hm = (t >> 8) & 0xff;
+          const float rp = A[hp], rm = A[hm], ip = A[nh + hp];
+          const float im = __int_as_float(__float_as_int(A[nh + hm]) ^ (unsigned(t >> 16) << 31));
+          reinterpret_cast<float4*>(qbuf)[j + kHalf * r] = make_float4(rp + rm, rp - rm, ip + im, ip - im);
         }
-        reinterpret_cast<float4*>(qbuf)[e] = make_float4(sr, dr, si, di);
       }
       if (j <= K) {
-        const int kx = j;
-        float qr, qi;
-        if (kx == 0) { qr = A[0]; qi = 0.f; }
-        else {
-          const int h0 = K + (kx - 1) * M + K + 1;
-          qr = A[h0];
-          qi = A[nh + h0];
-        }
-        reinterpret_cast<float2*>(qbuf + 4 * (K + 1) * K)[kx] = make_float2(qr, qi);
+        const int h0 = j == 0 ? 0 : K + (j - 1) * M + K + 1;
+        reinterpret_cast<float2*>(qbuf + 4 * (K + 1) * K)[j] = make_float2(A[h0], j == 0 ? 0.f : A[nh + h0]);
       }
     }
     __syncwarp();
@@ -181,9 +184,10 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
     }
     if (valid && j == 0) {
+      const int iy = int((float(bidx) + 0.5f) * invL), ix = bidx - iy * L;   // exact: bidx < 31^2
       a.vidx[pix] = bidx;
-      a.vx[pix] = -a.vmax + (bidx % L) * a.vstep;
-      a.vy[pix] = -a.vmax + (bidx / L) * a.vstep;
+      a.vx[pix] = -a.vmax + ix * a.vstep;
+      a.vy[pix] = -a.vmax + iy * a.vstep;
     }
     __syncwarp();
   }
@@ -195,7 +199,7 @@ cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
   constexpr int K = (M - 1) / 2;
   if (a.kpad != AcSmem<M>::kPad) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * size_t(kWarps) * 2 * (2 * AcSmem<M>::kPad + AcSmem<M>::kQ) +
-                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * ((a.L + 1) & ~1);
+                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * (2 * kHalf);
   const long long npix = (long long)a.H * a.W;
   long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
   if (blocks > 148LL * 8) blocks = 148LL * 8;

@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
   const int px = x0 + tx, py = y0 + ty;
   if (px >= W || py >= H) return;
   const size_t pix = size_t(py) * W + px;
-  const int g = a.vidx[pix];
+  int g = a.vidx[pix];
+  g = g < 0 ? 0 : (g >= L * L ? L * L - 1 : g);   // never index the tables out of range
   const int gx = g % L, gy = g / L;
   const float2* hw2 = reinterpret_cast<const float2*>(a.hw + pef_hw2_offset(L, MZ, M)) + size_t(gx) * MZ * M;
   const float2* hwp = reinterpret_cast<const float2*>(a.hw + pef_hwp_offset(L, MZ, M)) + size_t(gy) * MZ * K;
