@@ -16,9 +16,11 @@ other implementation of the method) on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -40,6 +42,47 @@ WORKLOAD = "512x640 IR stream, 15x15 window, temporal order 6, grid +-3 step 0.2
 L_GRID = int(round(2 * VMAX / VSTEP)) + 1
 U_BINS = (M * M * MZ + 2) // 2
 BYTES_PER_PX = 4 + 4 + 8 + 2 * 4 * MZ + 2 * 4 * min(L_GRID * L_GRID, U_BINS)
+# the same bytes by the kernel that moves them: the spectrum kernel reads the
+# frame, updates the observer state and the smoothed state; the search writes
+# the velocity; the PEF writes the whitened pixel
+KERNEL_BYTES_PER_PX = {
+    "spectrum": 4 + 2 * 4 * MZ + 2 * 4 * min(L_GRID * L_GRID, U_BINS),
+    "autocorr_argmax": 8,
+    "pef": 4,
+}
+assert sum(KERNEL_BYTES_PER_PX.values()) == BYTES_PER_PX
+# ncu summaries with the measured DRAM traffic of one launch at this workload,
+# and the kernel sources they were taken from (the figure is reported only
+# while those sources are unchanged)
+PROFILE_OF = {
+    "spectrum": ("profiles/spectrum_512x640_m15_mz6.md", ["k_spectrum.cu", "common.cuh"]),
+    "autocorr_argmax": ("profiles/autocorr_512x640_m15.md", ["k_autocorr.cu", "common.cuh"]),
+    "pef": ("profiles/pef_512x640_m15_mz6.md", ["k_pef.cu", "common.cuh"]),
+}
+
+
+def kernel_source_sha256(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1408_3526_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the kernel's ncu summary, or None when the
+    summary is missing or the kernel's sources changed since it was taken."""
+    md, srcs = PROFILE_OF[kernel]
+    try:
+        with open(os.path.join(ROOT, md)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m1 = re.search(r"^traffic_bytes_per_launch:\s*(\d+)", text, re.M)
+    m2 = re.search(r"^kernel_source_sha256:\s*([0-9a-f]{64})", text, re.M)
+    if not (m1 and m2) or m2.group(1) != kernel_source_sha256(srcs):
+        return None
+    return int(m1.group(1))
 
 
 def dist_env():
@@ -272,7 +315,7 @@ def main():
         # roofline of the whole path against HBM (all three kernels in one step)
         step_ms = ms_max / args.steps
         achieved_path = BYTES_PER_PX * H * W / (step_ms * 1e-3) / 1e9
-        achieved_dom = BYTES_PER_PX * H * W / (per[dom] * 1e-3) / 1e9
+        achieved_dom = KERNEL_BYTES_PER_PX[names[dom]] * H * W / (per[dom] * 1e-3) / 1e9
         line = {
             "metric": "whitened Mpixel/s (512x640 stream)",
             "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world,
@@ -286,7 +329,8 @@ def main():
                        "engine": "FP32-exact search on CUDA cores"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved_dom, 1),
                          "peak": hbm, "unit": "GB/s", "frac": round(achieved_dom / hbm, 4),
-                         "traffic": None, "peak_source": src,
+                         "traffic": measured_traffic(names[dom]), "peak_source": src,
+                         "bytes_per_launch_algorithmic": KERNEL_BYTES_PER_PX[names[dom]] * H * W,
                          "path_achieved": round(achieved_path, 1),
                          "path_frac": round(achieved_path / hbm, 4),
                          "kernel_ms": {n: round(p, 5) for n, p in zip(names, per)}},

@@ -61,6 +61,7 @@ struct SpecArgs {
   void* feat;
   int feat_ld;
   const int* feat_gather;
+  int* err;                     // device status word: set nonzero if a bounded wait gives up
 };
 
 struct AutocorrArgs {

@@ -41,6 +41,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace wh {
 
@@ -116,16 +117,26 @@ struct SG {
   static constexpr int GP = cdiv(GU, 32) * 32;
   static constexpr int NBT = (J + 1) * GP;                // x-DFT threads
   static constexpr int NDT = TW * NH1;                    // reduction tasks per row
-  // Reduction on the warps without x-DFT work, or on all warps, whichever has
-  // the shorter estimated critical path (x-DFT unit ~7 instr/tap, task ~28);
-  // never on the observer warp, which runs the box sums meanwhile.
+  // Reduction tasks: RD rounds on each thread without x-DFT work and RB rounds
+  // on each x-DFT thread, chosen for the shortest estimated critical path
+  // (x-DFT unit ~5.5 instr/tap, task ~25); never on the observer warp, which
+  // runs the box sums meanwhile.
   static constexpr int NTW = NTHR - 32;                   // threads other than the observer warp
-  static constexpr int BCOST = 7 * M + 12, DCOST = 28;
-  static constexpr int SPLIT_COST = (NBT < NTW) ? imax(BCOST, cdiv(NDT, NTW - NBT) * DCOST) : (1 << 30);
-  static constexpr int ALL_COST = BCOST + cdiv(NDT, NTW) * DCOST;
-  static constexpr int D0 = SPLIT_COST <= ALL_COST ? NBT : 0;   // first reduction thread
-  static constexpr int NDTHR = NTW - D0;
-  static constexpr int QD = cdiv(NDT, NDTHR);             // reduction rounds per row
+  static constexpr int NOB = NTW - NBT;                   // threads without x-DFT work
+  static constexpr int BCOST = 11 * M / 2 + 12, DCOST = 25;
+  static constexpr int rd_for(int rb) {
+    return NOB > 0 ? cdiv(imax(0, NDT - NBT * rb), NOB) : (NBT * rb >= NDT ? 0 : (1 << 20));
+  }
+  static constexpr int cost_for(int rb) { return imax(BCOST + rb * DCOST, rd_for(rb) * DCOST); }
+  static constexpr int pick_rb() {
+    int best = 0;
+    for (int rb = 1; rb <= 16; ++rb)
+      if (cost_for(rb) < cost_for(best)) best = rb;
+    return best;
+  }
+  static constexpr int RB = pick_rb();
+  static constexpr int RD = rd_for(RB);
+  static constexpr int SROW = TW * KPAD;                  // smoothed state of one output row segment
   // first channel of plane p (channel order: plane 0 kx = 0..K, complex planes
   // kx = -K..K, Nyquist plane kx = 0..K)
   __host__ __device__ static constexpr int base(int p) { return p == 0 ? 0 : (K + 1) + (p - 1) * M; }
@@ -134,14 +145,17 @@ struct SG {
   static constexpr size_t O_RING = al16(O_TWR + 8ull * NPL * RW);              // float2 [M+1][NCHY][TW]
   static constexpr size_t O_DCR = al16(O_RING + 8ull * (M + 1) * NCHY * TW);   // float2 [M+1][NPL][TW]
   static constexpr size_t O_XW = al16(O_DCR + 8ull * (M + 1) * NPL * TW);      // float2 [K+1][M]
-  static constexpr size_t O_PBUF = al16(O_XW + 8ull * (K + 1) * M);            // float  [TW][PS]
+  static constexpr size_t O_XW4 = al16(O_XW + 8ull * (K + 1) * M);             // float4 [K+1][M]
+  static constexpr size_t O_PBUF = al16(O_XW4 + 16ull * (K + 1) * M);          // float  [TW][PS]
   static constexpr size_t O_DBUF = al16(O_PBUF + 4ull * TW * PS);              // float2 [2][NPL][TW]
   static constexpr size_t O_ABUF = al16(O_DBUF + 8ull * 2 * NPL * TW);         // float  [RW][MZ+1]
-  static constexpr size_t O_DPRE = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [QD][2][NDTHR]
-  static constexpr size_t O_OFFS = al16(O_DPRE + 4ull * QD * 2 * NDTHR);       // float2 [NPL]
+  static constexpr size_t O_SROW = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [3][SROW]
+  static constexpr size_t O_MBAR = al16(O_SROW + 4ull * 3 * SROW);             // uint64 [3]
+  static constexpr size_t O_OFFS = al16(O_MBAR + 8ull * 3);                    // float2 [NPL]
   static constexpr size_t SMEM = al16(O_OFFS + 8ull * NPL);
   static_assert(RW <= 32, "the observer warp covers the row segment");
   static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
+  static_assert(NBT * RB + NOB * RD >= NDT, "every reduction task has a thread");
 };
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
@@ -226,7 +240,8 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   using G = SG<M, MZ>;
   constexpr int K = G::K, J = G::J, NPL = G::NPL, NCHY = G::NCHY;
   constexpr int TW = G::TW, RW = G::RW, NTHR = G::NTHR, PS = G::PS, KPAD = G::KPAD;
-  constexpr int NH = G::NH, NH1 = G::NH1, NDT = G::NDT, NDTHR = G::NDTHR, D0 = G::D0, QD = G::QD;
+  constexpr int NH = G::NH, NH1 = G::NH1, NDT = G::NDT, NTW = G::NTW, NBT = G::NBT, NOB = G::NOB;
+  constexpr int RB = G::RB, RD = G::RD;
   constexpr bool EVEN = G::EVEN;
   constexpr int MI = (M - 3) / 2, ZI = MZ - 3;
   constexpr int RING_SLOT = NCHY * TW, DC_SLOT = NPL * TW;
@@ -238,17 +253,27 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   float2* ring = reinterpret_cast<float2*>(smem_raw + G::O_RING);
   float2* dcr = reinterpret_cast<float2*>(smem_raw + G::O_DCR);
   float2* xw = reinterpret_cast<float2*>(smem_raw + G::O_XW);
+  float4* xw4 = reinterpret_cast<float4*>(smem_raw + G::O_XW4);
   float* pbuf = reinterpret_cast<float*>(smem_raw + G::O_PBUF);
   float2* dbuf = reinterpret_cast<float2*>(smem_raw + G::O_DBUF);
   float* abuf = reinterpret_cast<float*>(smem_raw + G::O_ABUF);
-  float* dpre = reinterpret_cast<float*>(smem_raw + G::O_DPRE);
+  float* srow = reinterpret_cast<float*>(smem_raw + G::O_SROW);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + G::O_MBAR);
   float2* offs = reinterpret_cast<float2*>(smem_raw + G::O_OFFS);
 
   // Power scale (Mz/sqrt(N))^2 and the 1/16 of the 4x Hann taps, as sig^2 on
   // the x-DFT weights and box sums (everything before the power is linear).
   const float sig = sqrtf(float(MZ) / float(16 * M * M));
-  for (int i = tid; i < (K + 1) * M; i += NTHR) xw[i] = cscale(a.tables->xcoef[i / M][i % M], sig);
+  for (int i = tid; i < (K + 1) * M; i += NTHR) {
+    const float2 w = cscale(a.tables->xcoef[i / M][i % M], sig);
+    xw[i] = w;                                   // (wr, wi)
+    xw4[i] = make_float4(w.x, w.x, w.y, w.y);    // (wr, wr, wi, wi)
+  }
   const float alpha = a.alpha, oma = 1.0f - alpha;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&mbar[b], 1);
+    tc::fence_mbar_init();
+  }
 
   // ---- static roles ---------------------------------------------------------
   // C: y-SDFT channel cy (plane plc, kx kxc) of column xy
@@ -267,9 +292,11 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   const bool owarp = tid >= NTHR - 32;
   const int ua = lane;
   const bool athr = owarp && ua < RW;
-  // D: reduction thread index
-  const bool dthr = tid >= D0 && tid < G::NTW;
-  const int dt = tid - D0;
+  // D: reduction tasks d = dbase + q * dstride, q < (x-DFT thread ? RB : RD)
+  const bool bown = tid < NBT;
+  const int dbase = bown ? NOB * RD + tid : tid - NBT;
+  const int dstride = bown ? NBT : NOB;
+  const bool dthr = tid < NTW;
 
   // ---- this CTA's share of the (strip, row) units -------------------------------
   const int nstrip = (W + TW - 1) / TW;
@@ -278,6 +305,11 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
   __syncthreads();
 
+  // Smoothed state of output rows: ring of 3 row segments in shared memory,
+  // moved by bulk copies issued by thread 0 (load two rows ahead, update in
+  // place, store back); the n-th use of slot b completes mbarrier phase n & 1.
+  int gbase = 0;                          // output rows this CTA finished in earlier segments
+  bool timed_out = false;
   for (long long u = u0; u < u1;) {
     const int strip = int(u / H);
     const int y0 = int(u % H);
@@ -323,7 +355,11 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
         if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
       }
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) twr[p * RW + ua] = csub(Tw[p], offs[p]);
+      for (int p = 0; p < NPL; ++p) {
+        const bool real = (p == 0) || (EVEN && p == NPL - 1);
+        const float2 v = csub(Tw[p], offs[p]);
+        twr[p * RW + ua] = real ? make_float2(v.x, v.x) : v;   // real planes as (v, v)
+      }
     };
     // whole observer warp: box sums along x of input row i (the (0,0) bin of
     // the row window at column ua), their running sum over the last M rows and
@@ -351,59 +387,57 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
         }
       }
     };
-    // phase-D prefetch of the smoother state of output row yo (own slots of dpre)
-    auto loadD = [&](int yo) {
-      if (dthr && yo < y1) {
-        const float* rowA = a.Astate + (size_t(yo) * W + x0) * KPAD;
-#pragma unroll
-        for (int q = 0; q < QD; ++q) {
-          const int d = dt + q * NDTHR;
-          if (d >= NDT) break;
-          const int x = d / NH1, hi = d - x * NH1;
-          if (x0 + x >= W) continue;
-          const float* src = rowA + x * KPAD + hi;
-          cp_async4(dpre + (2 * q) * NDTHR + dt, src);
-          if (hi > 0) cp_async4(dpre + (2 * q + 1) * NDTHR + dt, src + NH);
-        }
-      }
-      cp_async_commit();
+    // bulk copies of the smoothed state of output row r (relative to y0)
+    const int ncols = min(TW, W - x0);
+    const uint32_t row_bytes = uint32_t(ncols) * KPAD * 4u;   // a multiple of 16
+    auto row_slot = [&](int r) { return (gbase + r) % 3; };
+    auto load_row = [&](int r) {          // thread 0
+      const int b = row_slot(r);
+      const float* src = a.Astate + (size_t(y0 + r) * W + x0) * KPAD;
+      tc::mbar_expect_tx(&mbar[b], row_bytes);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+          ::"r"(tc::smem_u32(srow + b * G::SROW)), "l"(src), "r"(row_bytes), "r"(tc::smem_u32(&mbar[b]))
+          : "memory");
     };
+    auto store_row = [&](int r) {         // thread 0, after a CTA barrier
+      const int b = row_slot(r);
+      float* dst = a.Astate + (size_t(y0 + r) * W + x0) * KPAD;
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                   ::"l"(dst), "r"(tc::smem_u32(srow + b * G::SROW)), "r"(row_bytes) : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    };
+    const int TH = y1 - y0;
     auto doB = [&](int i) {               // x-DFT of input row i into ring slot i mod (M+1)
       if (!bthr) return;
       float2* rs = ring + (i % (M + 1)) * RING_SLOT;
-      const float2* w = xw + bkx * M;
-      if (bg == 0) {                      // real planes: real data, complex weights
+      if (bg == 0) {                      // real planes, stored (v, v): (wr, wi) x (v, v)
+        const float2* w = xw + bkx * M;
         const float2* r0 = twr + bx + 2 * K;
         const float2* r1 = twr + (NPL - 1) * RW + bx + 2 * K;
         float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int mx = 0; mx < M; ++mx) {
           const float2 cw = w[mx];
-          const float v0 = r0[-mx].x;
-          c0.x = fmaf(cw.x, v0, c0.x);
-          c0.y = fmaf(cw.y, v0, c0.y);
-          if (EVEN) {
-            const float v1 = r1[-mx].x;
-            c1.x = fmaf(cw.x, v1, c1.x);
-            c1.y = fmaf(cw.y, v1, c1.y);
-          }
+          c0 = __ffma2_rn(cw, r0[-mx], c0);
+          if (EVEN) c1 = __ffma2_rn(cw, r1[-mx], c1);
         }
         rs[bkx * TW + bx] = c0;                                   // channel (0, kx)
         if (EVEN) rs[(G::base(NPL - 1) + bkx) * TW + bx] = c1;    // channel (Mz/2, kx)
       } else {                            // complex plane bg: +kx and -kx together
+        const float4* w = xw4 + bkx * M;
         const float2* row = twr + bg * RW + bx + 2 * K;
-        float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
+        float2 ac = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);   // (sum wr vr, sum wr vi), (sum wi vr, sum wi vi)
 #pragma unroll
         for (int mx = 0; mx < M; ++mx) {
-          const float2 cw = w[mx], v = row[-mx];
-          pa = fmaf(cw.x, v.x, pa);
-          pb = fmaf(cw.y, v.y, pb);
-          pc = fmaf(cw.x, v.y, pc);
-          pd = fmaf(cw.y, v.x, pd);
+          const float4 cw = w[mx];
+          const float2 v = row[-mx];
+          ac = __ffma2_rn(make_float2(cw.x, cw.y), v, ac);
+          db = __ffma2_rn(make_float2(cw.z, cw.w), v, db);
         }
         const int c0 = G::base(bg) + K;                           // channel (bg, 0)
-        rs[(c0 + bkx) * TW + bx] = make_float2(pa - pb, pc + pd);
-        if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_float2(pa + pb, pc - pd);
+        rs[(c0 + bkx) * TW + bx] = make_float2(ac.x - db.y, ac.y + db.x);
+        if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_float2(ac.x + db.y, ac.y - db.x);
       }
     };
     auto doC = [&](int i) {               // y-SDFT, Hann(ky), high-pass, power of row i
@@ -470,17 +504,15 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       pb[K] = pwc;
       dump(K, zcx, zcy, pwc);
     };
-    auto doD = [&](int i) {               // reduce over kz, smooth, store (output row of i)
-      const int yo = y0 + i - 2 * K;
+    auto doD = [&](int i) {               // reduce over kz, smooth (in place in the row ring)
+      const int yo = y0 + i - 2 * K, r = i - 2 * K;
       if (!(i >= 2 * K && yo < y1) || !dthr) return;
-      cp_async_wait0();
-      float* rowA = a.Astate + (size_t(yo) * W + x0) * KPAD;
-#pragma unroll
-      for (int q = 0; q < QD; ++q) {
-        const int d = dt + q * NDTHR;
-        if (d >= NDT) break;
+      const int b = row_slot(r);
+      if (!tc::mbar_wait(&mbar[b], uint32_t(((gbase + r) / 3) & 1), 1000000000ull)) timed_out = true;
+      float* st = srow + b * G::SROW;
+      auto one = [&](int d) {
         const int x = d / NH1, hi = d - x * NH1;
-        if (x0 + x >= W) continue;
+        if (d >= NDT || x0 + x >= W) return;
         // P(h, kz) for the slots kz = 0, +j, -j (= P(-h, +j)), Mz/2 of this h:
         // offsets x*PS + (c*M + ky + K) with c the channel of (plane, +-hx)
         const int op = x * PS + hi + K, om = x * PS - hi + K;
@@ -492,16 +524,22 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
           As = fmaf(pp - pm, c_sz[ZI][j], As);
         }
         if (EVEN) Ac -= pbuf[op + G::base(NPL - 1) * M];
-        float* dst = rowA + x * KPAD + hi;
-        const float* pre = dpre + (2 * q) * NDTHR + dt;
-        dst[0] = fmaf(oma, Ac, alpha * pre[0]);
-        if (hi > 0) dst[NH] = fmaf(oma, As, alpha * pre[NDTHR]);
+        float* sp = st + x * KPAD + hi;
+        sp[0] = fmaf(oma, Ac, alpha * sp[0]);
+        if (hi > 0) sp[NH] = fmaf(oma, As, alpha * sp[NH]);
+      };
+      if (bown) {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) one(dbase + q * dstride);
+      } else {
+#pragma unroll
+        for (int q = 0; q < RD; ++q) one(dbase + q * dstride);
       }
-      loadD(yo + 1);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the bulk store
       // learned-estimator features of this output row: one warp per pixel
       if (a.feat != nullptr) {
-        constexpr int NDW = NDTHR / 32;
-        const int wid = dt >> 5;
+        constexpr int NDW = NTW / 32;
+        const int wid = tid >> 5;
         constexpr int nbins = M * M * MZ;
         for (int x = wid; x < TW; x += NDW) {
           if (x0 + x >= W) continue;
@@ -536,7 +574,10 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
 #pragma unroll
       for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
     }
-    loadD(y0);
+    if (tid == 0) {
+      load_row(0);
+      if (TH > 1) load_row(1);
+    }
     __syncthreads();
     cp_async_wait0();
     if (owarp) {
@@ -551,6 +592,14 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     // ---- pipelined rows: {y-SDFT(i), observer(i+1)},
     //      {reduce(i), x-DFT(i+1), box sums(i+1)}
     for (int i = 0; i < nrows; ++i) {
+      if (tid == 0 && i > 2 * K && i - 1 - 2 * K < TH) {
+        // the previous iteration finished output row rp: store it, then reuse
+        // the slot of row rp - 1 (its store has read it) for row rp + 2
+        const int rp = i - 1 - 2 * K;
+        store_row(rp);
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        if (rp + 2 < TH) load_row(rp + 2);
+      }
       doC(i);
       if (owarp && i + 1 < nrows) {
         cp_async_wait0();
@@ -565,9 +614,15 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       }
       __syncthreads();
     }
+    if (tid == 0) {
+      store_row(TH - 1);
+      asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+    gbase += TH;
     cp_async_wait0();
-    __syncthreads();   // before the next segment rewrites offs
+    __syncthreads();   // before the next segment rewrites offs and the row ring
   }
+  if (timed_out && a.err) atomicExch(a.err, 1);
 }
 
 template <int M, int MZ>

@@ -126,6 +126,7 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
   sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
+  sa.err = s->d_err;
   e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return wh_cuda_fail(e, "spectrum kernel");
   // 2. autocorrelation search with all scratch in the static array

@@ -274,6 +274,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   alloc((void**)&s->vy, sizeof(float) * npix);
   alloc((void**)&s->vidx, sizeof(int) * npix);
   alloc((void**)&s->d_spec, sizeof(SpecTables));
+  alloc((void**)&s->d_err, sizeof(int));
   if (s->debug) {
     alloc((void**)&s->d_dump_win, sizeof(float2) * npix * M * M * Mz);
     alloc((void**)&s->d_dump_pow, sizeof(float) * npix * M * M * Mz);
@@ -331,6 +332,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     return rc;
   }
   cudaError_t c1 = cudaMemcpy(s->d_spec, &tb, sizeof(tb), cudaMemcpyHostToDevice);
+  if (c1 == cudaSuccess) c1 = cudaMemset(s->d_err, 0, sizeof(int));
   cudaError_t c2 = cudaMemcpy(s->d_hgather, hg.data(), sizeof(int) * hg.size(), cudaMemcpyHostToDevice);
   cudaError_t c3 = cudaMemcpy(s->d_taby, taby.data(), sizeof(float2) * taby.size(), cudaMemcpyHostToDevice);
   cudaError_t c4 = cudaMemcpy(s->d_tabx, tabx.data(), sizeof(float2) * tabx.size(), cudaMemcpyHostToDevice);
@@ -348,7 +350,6 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     alloc((void**)&s->d_cval, sizeof(float) * npix * nc);
     alloc((void**)&s->d_cidx, sizeof(int) * npix * nc);
     alloc((void**)&s->d_table, 2 * size_t(s->ntile) * 128 * s->kg);
-    alloc((void**)&s->d_err, sizeof(int));
     alloc((void**)&s->d_nfb, sizeof(int));
     if (e != cudaSuccess) {
       int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "cudaMalloc");
@@ -385,7 +386,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
       }
     }
     cudaError_t c6 = cudaMemcpy(s->d_table, tb16.data(), 2 * tb16.size(), cudaMemcpyHostToDevice);
-    cudaError_t c7 = cudaMemset(s->d_err, 0, sizeof(int));
+    cudaError_t c7 = cudaSuccess;
     cudaError_t c8 = cudaMemset(s->d_nfb, 0, sizeof(int));
     cudaError_t c9 = cudaMemset(s->d_a16, 0, 2 * npix * s->kg);
     for (cudaError_t c : {c6, c7, c8, c9})
@@ -448,6 +449,7 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
   sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
+  sa.err = s->d_err;
   cudaError_t e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
   if (ev) WH_CU(cudaEventRecord(ev[1], s->st));
@@ -490,12 +492,26 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   return WH_OK;
 }
 
+// After a synchronisation: the device status word is nonzero if a bounded
+// wait inside one of this stream's kernels gave up (the results of that frame
+// are not valid); reported once as WH_ECUDA.
+static int check_device_status(wh_stream* s) {
+  int h = 0;
+  WH_CU(cudaMemcpy(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    cudaMemset(s->d_err, 0, sizeof(int));
+    return wh_cuda_fail(cudaErrorLaunchTimeout, "a device-side wait timed out");
+  }
+  return WH_OK;
+}
+
 static int copy_out(wh_stream* s, void* dst, const void* src, size_t bytes, int is_device) {
   if (is_device) {
     WH_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s->st));
   } else {
     WH_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->st));
     WH_CU(cudaStreamSynchronize(s->st));
+    return check_device_status(s);
   }
   return WH_OK;
 }
@@ -568,12 +584,10 @@ int wh_stream_info(const wh_stream* s, int* grid_len, int* delay_z, int* band,
 int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
   if (!s) return WH_EINVAL;
   int h = 0;
-  if (s->d_nfb) {
-    WH_CU(cudaMemcpyAsync(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-    WH_CU(cudaStreamSynchronize(s->st));
-  }
+  WH_CU(cudaStreamSynchronize(s->st));
+  if (s->d_nfb) WH_CU(cudaMemcpy(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost));
   if (fallback_pixels) *fallback_pixels = h;
-  return WH_OK;
+  return check_device_status(s);
 }
 
 int wh_stream_set_features(wh_stream* s, int enable) {
