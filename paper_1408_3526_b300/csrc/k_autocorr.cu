@@ -40,7 +40,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-template <int M, bool RS>
+// LP: row stride of the T buffer (even, >= L): 26 covers the common grids up
+// to L = 25 and lets three blocks share an SM; 32 covers L <= 31.
+template <int M, bool RS, int LP>
 __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArgs a) {
   constexpr int K = (M - 1) / 2;
   constexpr int QN = AcSmem<M>::kQ, KP = AcSmem<M>::kPad;
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   float* sbase = reinterpret_cast<float*>(smem_raw);
   float* abuf = sbase + hw * 2 * KP;                                                    // [2][KP]
   float* qbuf = sbase + kWarps * 2 * 2 * KP + hw * QN;                                  // [QN]
-  constexpr int Lp = 2 * kHalf;   // row stride (>= L, even: rows gy, gy+1 load as one float4)
+  constexpr int Lp = LP;          // row stride (>= L, even: rows gy, gy+1 load as one float4)
   float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * (K + 1) * Lp;   // [K+1][Lp]
   // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
   float2 cs[K];
@@ -194,20 +196,25 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int M>
-cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
+template <int M, int LP>
+cudaError_t launch_mp(const AutocorrArgs& a, cudaStream_t st) {
   constexpr int K = (M - 1) / 2;
-  if (a.kpad != AcSmem<M>::kPad) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * size_t(kWarps) * 2 * (2 * AcSmem<M>::kPad + AcSmem<M>::kQ) +
-                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * (2 * kHalf);
+                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * LP;
   const long long npix = (long long)a.H * a.W;
   long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
   if (blocks > 148LL * 8) blocks = 148LL * 8;
-  auto kern = a.rs_out ? autocorr_kernel<M, true> : autocorr_kernel<M, false>;
+  auto kern = a.rs_out ? autocorr_kernel<M, true, LP> : autocorr_kernel<M, false, LP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   kern<<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
+  if (a.kpad != AcSmem<M>::kPad) return cudaErrorInvalidValue;
+  return a.L <= 25 ? launch_mp<M, 26>(a, st) : launch_mp<M, 2 * kHalf>(a, st);
 }
 
 }  // namespace
