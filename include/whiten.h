@@ -118,6 +118,51 @@ int wh_create_stream(int frame_h, int frame_w, int window, int temporal_order,
 int wh_push_frame(wh_stream *s, const float *frame, int is_device);
 
 /*
+ * Pipelined push for streaming from host memory: enqueues the copy of the
+ * host frame to the device, the whole per-pixel path of wh_push_frame for it,
+ * and the copies of its whitened pixel and velocity back to the host, then
+ * returns without waiting.  The copies run on two internal CUDA streams and
+ * the stream keeps two sets of device frame/output buffers, so the copies of
+ * one frame overlap the kernels of the next (ordering by CUDA events).
+ *   frame_host         float32 [h][w], page-locked host memory; must stay
+ *                      unchanged until the frame has been consumed (after the
+ *                      next call returns, or after wh_stream_sync)
+ *   whitened_host      NULL or float32 [h][w] page-locked: the whitened pixel
+ *                      of frame *frame_index - delay_z (zeros while fewer
+ *                      than delay_z + 1 frames were pushed)
+ *   vx_host, vy_host   NULL or float32 [h][w] page-locked: the velocity of
+ *                      frame *frame_index
+ *   frame_index        NULL or receives the index of the frame just pushed
+ * The host outputs are complete once wh_stream_query_frame(s, index, 1) or
+ * wh_stream_sync(s) returns WH_OK.  After asynchronous pushes, call
+ * wh_stream_sync before wh_read_* with host destinations if their results
+ * are needed in program order.  The paper has no counterpart (it is I/O
+ * plumbing around Sec. 1-2's per-frame path).
+ * Errors: WH_EINVAL (NULL), WH_ENOMEM (first call allocates the second
+ * buffer set, 4 * h * w floats), WH_ECUDA.
+ */
+int wh_push_frame_async(wh_stream *s, const float *frame_host, float *whitened_host, float *vx_host,
+                        float *vy_host, long long *frame_index);
+
+/*
+ * Wait until every kernel and copy enqueued on the stream (including
+ * asynchronous pushes) has finished.  Returns WH_ECUDA if a bounded
+ * device-side wait gave up since the last check (the frame's results are then
+ * not valid).
+ * Errors: WH_EINVAL (NULL), WH_ECUDA.
+ */
+int wh_stream_sync(wh_stream *s);
+
+/*
+ * Whether the host outputs of frame frame_index (from wh_push_frame_async)
+ * are complete: wait = 1 blocks until they are and returns WH_OK; wait = 0
+ * returns WH_OK or WH_ENOTREADY.  Frames pushed with wh_push_frame report
+ * WH_OK.
+ * Errors: WH_EINVAL (NULL, or an index never pushed), WH_ECUDA.
+ */
+int wh_stream_query_frame(wh_stream *s, long long frame_index, int wait);
+
+/*
  * Allocation-free variant of wh_push_frame.  The paper has no counterpart; it
  * exists for callers that cannot allocate device memory once streaming has
  * started (fixed-memory real-time loops, allocation-free pools, hosts that

@@ -61,6 +61,9 @@ _SIGS = {
                                    C.POINTER(wh_params), _VP, C.POINTER(_VP)]),
     "wh_push_frame": (C.c_int, [_VP, _VP, C.c_int]),
     "wh_push_frame_noalloc": (C.c_int, [_VP, _VP, C.c_int]),
+    "wh_push_frame_async": (C.c_int, [_VP, _VP, _VP, _VP, _VP, C.POINTER(C.c_longlong)]),
+    "wh_stream_sync": (C.c_int, [_VP]),
+    "wh_stream_query_frame": (C.c_int, [_VP, C.c_longlong, C.c_int]),
     "wh_read_whitened": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(C.c_longlong)]),
     "wh_read_velocity": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, C.POINTER(C.c_longlong)]),
     "wh_read_spectrum": (C.c_int, [_VP, C.c_int, _VP, C.c_int]),

@@ -181,8 +181,27 @@ static void fill_tc_args(const wh_stream* s, AutocorrTcArgs& ta) {
   ta.vidx = s->vidx; ta.vx = s->vx; ta.vy = s->vy; ta.tab_x = s->d_tabx; ta.n_fallback = s->d_nfb;
 }
 
+static void free_async(wh_stream* s) {
+  wh_stream::Async* a = s->as;
+  if (!a) return;
+  if (a->in) cudaStreamSynchronize(a->in);
+  if (a->out) cudaStreamSynchronize(a->out);
+  // set 0 is the stream's own buffers (freed with the stream), set 1 was added
+  s->frame = a->frame[0]; s->whitened = a->w[0]; s->vx = a->vx[0]; s->vy = a->vy[0];
+  for (void* p : {(void*)a->frame[1], (void*)a->w[1], (void*)a->vx[1], (void*)a->vy[1]})
+    if (p) cudaFree(p);
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t e : {a->ev_in[b], a->ev_comp[b], a->ev_out[b]})
+      if (e) cudaEventDestroy(e);
+  if (a->in) cudaStreamDestroy(a->in);
+  if (a->out) cudaStreamDestroy(a->out);
+  delete a;
+  s->as = nullptr;
+}
+
 static void free_stream(wh_stream* s) {
   if (!s) return;
+  free_async(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
@@ -246,6 +265,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->d_feat = nullptr; s->feat_ld = 0; s->d_fgather = nullptr; s->mlp = nullptr; s->conf_thr = 0.8f;
   s->d_ymlp = nullptr; s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
   s->mlp_frames = 0;
+  s->as = nullptr;
   s->tc_mode = pmode == 0 ? 0 : 1;
   s->tc_bf16 = pmode == 2 ? 1 : 0;
   s->use_tc = (pmode != 0) || ((p.precision & WH_PREC_TC_SHORTLIST) && autocorr_tc_supported(M));
@@ -423,14 +443,11 @@ int wh_reset_stream(wh_stream* s) {
   return WH_OK;
 }
 
-int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
-  if (!s || !frame) return WH_EINVAL;
-  const size_t npix = size_t(s->H) * s->W;
-  const float* src = frame;
-  if (!is_device) {
-    WH_CU(cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, s->st));
-    src = s->frame;
-  }
+static int check_device_status(wh_stream* s);
+
+// The three kernels of one frame on s->st, reading the device frame src and
+// writing s->whitened / s->vx / s->vy / s->vidx.
+static int push_kernels(wh_stream* s, const float* src) {
   cudaEvent_t* ev = nullptr;
   if (s->prof && s->ev_used + 4 <= 4 * 65536) {
     while (s->ev.size() < s->ev_used + 4) {
@@ -489,6 +506,110 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   g_launches.fetch_add(nlaunch);
   s->cur = 1 - s->cur;
   s->t += 1;
+  return WH_OK;
+}
+
+int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
+  if (!s || !frame) return WH_EINVAL;
+  const size_t npix = size_t(s->H) * s->W;
+  const float* src = frame;
+  if (s->as) {   // the buffers in use may still be read by an asynchronous output copy
+    for (int b = 0; b < 2; ++b)
+      if (s->as->used[b]) WH_CU(cudaStreamWaitEvent(s->st, s->as->ev_out[b], 0));
+  }
+  if (!is_device) {
+    WH_CU(cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, s->st));
+    src = s->frame;
+  }
+  return push_kernels(s, src);
+}
+
+static int init_async(wh_stream* s) {
+  if (s->as) return WH_OK;
+  wh_stream::Async* a = new wh_stream::Async{};
+  s->as = a;
+  const size_t bytes = sizeof(float) * size_t(s->H) * s->W;
+  a->frame[0] = s->frame; a->w[0] = s->whitened; a->vx[0] = s->vx; a->vy[0] = s->vy;
+  cudaError_t e = cudaSuccess;
+  for (float** p : {&a->frame[1], &a->w[1], &a->vx[1], &a->vy[1]})
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a->w[1], 0, bytes, s->st);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a->in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a->out, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    for (cudaEvent_t* ev : {&a->ev_in[b], &a->ev_comp[b], &a->ev_out[b]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_async(s);
+    return e == cudaErrorMemoryAllocation ? WH_ENOMEM : wh_cuda_fail(e, "asynchronous push set-up");
+  }
+  return WH_OK;
+}
+
+int wh_push_frame_async(wh_stream* s, const float* frame_host, float* whitened_host, float* vx_host,
+                        float* vy_host, long long* frame_index) {
+  if (!s || !frame_host) return WH_EINVAL;
+  int rc = init_async(s);
+  if (rc != WH_OK) return rc;
+  wh_stream::Async* a = s->as;
+  const int b = a->par;
+  const size_t bytes = sizeof(float) * size_t(s->H) * s->W;
+  // input copy: the set's frame buffer was last read by the kernels of the
+  // push before the previous one
+  if (a->used[b]) WH_CU(cudaStreamWaitEvent(a->in, a->ev_comp[b], 0));
+  WH_CU(cudaMemcpyAsync(a->frame[b], frame_host, bytes, cudaMemcpyHostToDevice, a->in));
+  WH_CU(cudaEventRecord(a->ev_in[b], a->in));
+  // kernels: after the input copy, and after the set's previous outputs were copied out
+  WH_CU(cudaStreamWaitEvent(s->st, a->ev_in[b], 0));
+  if (a->used[b]) WH_CU(cudaStreamWaitEvent(s->st, a->ev_out[b], 0));
+  s->frame = a->frame[b]; s->whitened = a->w[b]; s->vx = a->vx[b]; s->vy = a->vy[b];
+  rc = push_kernels(s, a->frame[b]);
+  if (rc != WH_OK) return rc;
+  WH_CU(cudaEventRecord(a->ev_comp[b], s->st));
+  // output copies
+  WH_CU(cudaStreamWaitEvent(a->out, a->ev_comp[b], 0));
+  if (whitened_host) WH_CU(cudaMemcpyAsync(whitened_host, a->w[b], bytes, cudaMemcpyDeviceToHost, a->out));
+  if (vx_host) WH_CU(cudaMemcpyAsync(vx_host, a->vx[b], bytes, cudaMemcpyDeviceToHost, a->out));
+  if (vy_host) WH_CU(cudaMemcpyAsync(vy_host, a->vy[b], bytes, cudaMemcpyDeviceToHost, a->out));
+  WH_CU(cudaEventRecord(a->ev_out[b], a->out));
+  a->used[b] = 1;
+  a->frame_of[b] = s->t - 1;
+  a->par = 1 - b;
+  if (frame_index) *frame_index = s->t - 1;
+  return WH_OK;
+}
+
+int wh_stream_sync(wh_stream* s) {
+  if (!s) return WH_EINVAL;
+  WH_CU(cudaStreamSynchronize(s->st));
+  if (s->as) {
+    WH_CU(cudaStreamSynchronize(s->as->in));
+    WH_CU(cudaStreamSynchronize(s->as->out));
+  }
+  return check_device_status(s);
+}
+
+int wh_stream_query_frame(wh_stream* s, long long frame_index, int wait) {
+  if (!s || frame_index < 0 || frame_index >= s->t) return WH_EINVAL;
+  wh_stream::Async* a = s->as;
+  if (!a) return WH_OK;                       // no asynchronous push made
+  // output copies run in order on one stream: the oldest tracked push at or
+  // after frame_index completes after it
+  cudaEvent_t ev = nullptr;
+  long long best = 0;
+  for (int b = 0; b < 2; ++b)
+    if (a->used[b] && a->frame_of[b] >= frame_index && (ev == nullptr || a->frame_of[b] < best)) {
+      best = a->frame_of[b];
+      ev = a->ev_out[b];
+    }
+  if (!ev) return WH_OK;                      // pushed synchronously
+  if (wait) {
+    WH_CU(cudaEventSynchronize(ev));
+    return check_device_status(s);
+  }
+  const cudaError_t q = cudaEventQuery(ev);
+  if (q == cudaErrorNotReady) return WH_ENOTREADY;
+  if (q != cudaSuccess) return wh_cuda_fail(q, "cudaEventQuery");
   return WH_OK;
 }
 

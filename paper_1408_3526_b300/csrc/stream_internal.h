@@ -51,6 +51,20 @@ struct wh_stream {
   int* d_nlist;          // [1]
   long long* d_nfb_total;// fallback pixels accumulated
   long long mlp_frames;
+  // asynchronous pipelined push (wh_push_frame_async): two sets of frame and
+  // output buffers (set 0 is the stream's own), copy streams and events
+  struct Async {
+    float* frame[2];
+    float* w[2];
+    float* vx[2];
+    float* vy[2];
+    cudaStream_t in, out;
+    cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+    int used[2];               // the set's events have been recorded
+    long long frame_of[2];     // frame index last pushed with the set
+    int par;                   // set of the next push
+  };
+  Async* as;
   // per-kernel timing (wh_profile_enable)
   int prof;
   std::vector<cudaEvent_t> ev;   // 4 per timed frame

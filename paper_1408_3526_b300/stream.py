@@ -106,6 +106,29 @@ class WhitenStream:
         ptr, dev = _ptr_of(frame)
         check(self.lib.wh_push_frame(self._s, C.c_void_p(ptr), dev), "wh_push_frame")
 
+    def push_async(self, frame, whitened=None, vx=None, vy=None) -> int:
+        """Pipelined push from page-locked host memory (wh_push_frame_async).
+
+        frame, whitened, vx, vy: pinned CPU torch tensors of shape (H, W)
+        (outputs may be None).  Returns the frame index; the outputs are
+        complete after wait_frame(index) or sync()."""
+        def p(t):
+            if t is None:
+                return None
+            if not (t.is_pinned() and t.is_contiguous()):
+                raise ValueError("asynchronous push needs contiguous pinned host tensors")
+            return C.c_void_p(t.data_ptr())
+        idx = C.c_longlong()
+        check(self.lib.wh_push_frame_async(self._s, p(frame), p(whitened), p(vx), p(vy), C.byref(idx)),
+              "wh_push_frame_async")
+        return int(idx.value)
+
+    def wait_frame(self, index: int) -> None:
+        check(self.lib.wh_stream_query_frame(self._s, C.c_longlong(index), 1), "wh_stream_query_frame")
+
+    def sync(self) -> None:
+        check(self.lib.wh_stream_sync(self._s), "wh_stream_sync")
+
     def _alloc(self, shape, dtype, device):
         if device:
             torch = _torch()
