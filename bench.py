@@ -92,6 +92,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """Largest value of x over the ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpx_per_s(world, frames_per_rank, seconds):
+    """Pixels processed by all ranks divided by the slowest rank's time."""
+    return world * H * W * frames_per_rank / seconds / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -276,11 +292,8 @@ def main():
     ms = e0.elapsed_time(e1)
     kms, nprof = s.profile_read(reset=True)
     s.profile(False)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * H * W * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_mpx_per_s(world, args.steps, ms_max * 1e-3)
 
     # end to end through the C ABI: pinned host frame in, whitened + velocity out
     pin_in = torch.from_numpy(frames_h[:8].copy()).pin_memory()
@@ -307,10 +320,7 @@ def main():
         assert rc == 0
     assert lib.wh_stream_sync(s._s) == 0
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = world * H * W * args.e2e_steps / float(e2e_t.item()) / 1e6
+    e2e_val = whole_job_mpx_per_s(world, args.e2e_steps, max_over_ranks(e2e_s, world, "cuda"))
 
     if rank == 0:
         hbm, src = peaks()
