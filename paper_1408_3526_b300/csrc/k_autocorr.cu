@@ -19,6 +19,7 @@
 // and reads T(., ly) by broadcast, two ly rows per 16-byte load.  The
 // (cos, sin) x (re, im) products run as packed FP32x2 FMAs, each component
 // rounded exactly as fmaf.
+#include "ac_common.cuh"
 #include "common.cuh"
 
 namespace wh {
@@ -29,16 +30,9 @@ constexpr int kHalf = 16;   // lanes per pixel; the grid half-length (L+1)/2 mus
 
 template <int M>
 struct AcSmem {
-  static constexpr int K = (M - 1) / 2;
-  // per pixel: Q sums [K+1][K] x 4 (sr, dr, si, di) + Q(kx,0) [K+1] x 2
-  static constexpr int kQ = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;   // 16-byte multiple
-  static constexpr int kPad = (M * M + 3) & ~3;                          // state row (floats)
+  static constexpr int kQ = ac::Geo<M>::QN;
+  static constexpr int kPad = ac::Geo<M>::KP;
 };
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 
 // LP: row stride of the T buffer (even, >= L): 26 covers the common grids up
 // to L = 25 and lets three blocks share an SM; 32 covers L <= 31.
@@ -46,7 +40,7 @@ template <int M, bool RS, int LP>
 __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArgs a) {
   constexpr int K = (M - 1) / 2;
   constexpr int QN = AcSmem<M>::kQ, KP = AcSmem<M>::kPad;
-  const int L = a.L, Lh = (L + 1) / 2, gc = (L - 1) / 2, nh = (M * M - 1) / 2;
+  const int L = a.L, Lh = (L + 1) / 2, gc = (L - 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int half = lane >> 4, j = lane & 15;
   const int hw = wid * 2 + half;                        // half-warp (pixel slot) in the block
@@ -61,20 +55,9 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   const bool act = j < Lh;
 #pragma unroll
   for (int k = 0; k < K; ++k) cs[k] = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
-  // Q-sum elements e = j + 16 r of this lane: offsets hp, hm of A(kx, +ky) and
-  // A(kx, -ky) in the half-plane state, and a sign bit that conjugates the
-  // second one for kx = 0 (A(0, -ky) = conj A(0, ky) is stored as A(0, ky))
-  constexpr int NE = (K + 1) * K, QIT = (NE + kHalf - 1) / kHalf;
+  constexpr int QIT = (ac::Geo<M>::NE + kHalf - 1) / kHalf;
   int qoff[QIT];
-#pragma unroll
-  for (int r = 0; r < QIT; ++r) {
-    const int e = j + kHalf * r;
-    const int kx = e / K, ky = e % K + 1;
-    int hp, hm, neg;
-    if (kx == 0) { hp = ky; hm = ky; neg = 1; }
-    else { hp = K + (kx - 1) * M + (ky + K) + 1; hm = K + (kx - 1) * M + (-ky + K) + 1; neg = 0; }
-    qoff[r] = e < NE ? (hp | (hm << 8) | (neg << 16)) : -1;
-  }
+  ac::qsum_offsets<M, QIT>(j, qoff);
   const float invL = 1.0f / float(L);
   const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
   const long long stride = (long long)gridDim.x * kWarps * 2;
@@ -83,11 +66,7 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   };
   // the state row of this half-warp's pixel at b -> abuf slot (16-byte copies)
   auto prefetch = [&](long long b, int slot) {
-    if (b < npix) {
-      const float* src = a.Astate + pixel_of(b) * KP;
-      for (int c = j; c < KP / 4; c += kHalf) cp_async16(abuf + slot * KP + 4 * c, src + 4 * c);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    ac::prefetch_row<M>(abuf + slot * KP, a.Astate + (b < npix ? pixel_of(b) : 0) * KP, j, b < npix);
   };
   long long base = ((long long)blockIdx.x * kWarps + wid) * 2;
   prefetch(base + half, 0);
@@ -98,23 +77,7 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
     __syncwarp();
     prefetch(base + stride + half, (it + 1) & 1);
     // ---- Q sums of this half-warp's pixel ----------------------------------
-    if (valid) {
-      const float* A = abuf + (it & 1) * KP;
-#pragma unroll
-      for (int r = 0; r < QIT; ++r) {
-        const int t = qoff[r];
-        if (t >= 0) {
-          const int hp = t & 0xff, hm = (t >> 8) & 0xff;
-          const float rp = A[hp], rm = A[hm], ip = A[nh + hp];
-          const float im = __int_as_float(__float_as_int(A[nh + hm]) ^ (unsigned(t >> 16) << 31));
-          reinterpret_cast<float4*>(qbuf)[j + kHalf * r] = make_float4(rp + rm, rp - rm, ip + im, ip - im);
-        }
-      }
-      if (j <= K) {
-        const int h0 = j == 0 ? 0 : K + (j - 1) * M + K + 1;
-        reinterpret_cast<float2*>(qbuf + 4 * (K + 1) * K)[j] = make_float2(A[h0], j == 0 ? 0.f : A[nh + h0]);
-      }
-    }
+    if (valid) ac::build_qsums<M, QIT>(abuf + (it & 1) * KP, qbuf, qoff, j);
     __syncwarp();
     // ---- stage 1: T(kx, +-ly_j) ---------------------------------------------
     if (valid && act) {

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "ac_common.cuh"
 #include "common.cuh"
 
 namespace wh {
@@ -74,137 +75,103 @@ __global__ void __launch_bounds__(256) ac_convert_kernel(const AutocorrTcArgs a)
   }
 }
 
-// Exact FP32 R at flat grid index g from the pixel's Q sums (layout as in
-// the CUDA-core search: [K+1][K] x (sr, dr, si, di), then Q(kx,0)).
+// Re-rank: two pixels per warp (a half-warp each).  The pixel's state row
+// arrives by cp.async one pixel ahead (double buffer), its Q sums are built in
+// shared memory, and lane j evaluates shortlist entries j, j + 16, ... exactly
+// (ac::exact_R: the same FP32 sequence as the CUDA-core search, so the result
+// equals that search's whenever the shortlist holds its argmax).
 template <int M>
-__device__ __forceinline__ float exact_R(const float* qbuf, const float2* tabx, int L, int g) {
-  constexpr int K = (M - 1) / 2;
-  const int gc = (L - 1) / 2;
-  const int gy = g / L, gx = g % L;
-  const int jy = gy - gc, jx = gx - gc;
-  const float2* ty = tabx + (gc + (jy < 0 ? -jy : jy)) * (K + 1);   // cos/sin(2pi k |ly|/M)
-  const float2* tx = tabx + (gc + (jx < 0 ? -jx : jx)) * (K + 1);
-  const float4* q4 = reinterpret_cast<const float4*>(qbuf);
-  const float2* q0 = reinterpret_cast<const float2*>(qbuf + 4 * (K + 1) * K);
-  float ry[K], iy[K];                 // cos/sin(2pi ky |ly|/M), ky = 1..K
-#pragma unroll
-  for (int ky = 0; ky < K; ++ky) { const float2 w = ty[ky + 1]; ry[ky] = w.x; iy[ky] = w.y; }
-  float t0r = 0.f, v1 = 0.f, v2 = 0.f;
-#pragma unroll 1
-  for (int kx = 0; kx <= K; ++kx) {
-    const float2 z = q0[kx];
-    float va = z.x, vb = 0.f, vc = 0.f, vd = z.y;
-#pragma unroll
-    for (int ky = 0; ky < K; ++ky) {
-      const float4 q = q4[kx * K + ky];
-      va = fmaf(q.x, ry[ky], va);
-      vb = fmaf(q.w, iy[ky], vb);
-      vc = fmaf(q.y, iy[ky], vc);
-      vd = fmaf(q.z, ry[ky], vd);
-    }
-    const float tr = jy >= 0 ? va - vb : va + vb;
-    const float ti = jy >= 0 ? vc + vd : vd - vc;
-    if (kx == 0) t0r = tr;
-    else {
-      const float2 w = tx[kx];
-      v1 = fmaf(w.x, tr, v1);
-      v2 = fmaf(w.y, ti, v2);
-    }
-  }
-  return jx >= 0 ? fmaf(2.f, v1 - v2, t0r) : fmaf(2.f, v1 + v2, t0r);
-}
-
-template <int M>
-__global__ void __launch_bounds__(kWarpsR * 32, 4) ac_rerank_kernel(const AutocorrTcArgs a) {
-  constexpr int K = (M - 1) / 2;
-  constexpr int QN = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;
-  const int L = a.L, nh = (M * M - 1) / 2, ncand = a.ncand, og = a.ovf_group;
+__global__ void __launch_bounds__(kWarpsR * 32) ac_rerank_kernel(const AutocorrTcArgs a) {
+  using G = ac::Geo<M>;
+  constexpr int QN = G::QN, KP = G::KP, K = G::K;
+  constexpr int QIT = (G::NE + 15) / 16;
+  const int L = a.L, ncand = a.ncand, og = a.ovf_group;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int half = lane >> 4, j = lane & 15;
+  const int hw = wid * 2 + half;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tabx = reinterpret_cast<float2*>(smem_raw);                            // [L][K+1]
-  float* qbuf = reinterpret_cast<float*>(tabx + ((L * (K + 1) + 1) & ~1)) + wid * QN;
+  float* sbase = reinterpret_cast<float*>(smem_raw);
+  float* abuf = sbase + hw * 2 * KP;                                   // [2][KP]
+  float* qbuf = sbase + kWarpsR * 2 * 2 * KP + hw * QN;                // [QN]
+  float2* tabx = reinterpret_cast<float2*>(sbase + kWarpsR * 2 * (2 * KP + QN));   // [L][K+1]
   for (int i = threadIdx.x; i < L * (K + 1); i += blockDim.x) tabx[i] = a.tab_x[i];
   __syncthreads();
+  int qoff[QIT];
+  ac::qsum_offsets<M, QIT>(j, qoff);
+  const float invL = 1.0f / float(L);
   const long long npix = (long long)a.H * a.W;
-  for (long long pix = (long long)blockIdx.x * kWarpsR + wid; pix < npix;
-       pix += (long long)gridDim.x * kWarpsR) {
-    // shortlist
-    float cv = -INFINITY;
-    int ci = 0x7fffffff;
-    if (lane < ncand) {
-      cv = a.cand_val[pix * ncand + lane];
-      ci = a.cand_idx[pix * ncand + lane];
+  const long long stride = (long long)gridDim.x * kWarpsR * 2;
+  long long base = ((long long)blockIdx.x * kWarpsR + wid) * 2;
+  ac::prefetch_row<M>(abuf, a.Astate + (base + half < npix ? base + half : 0) * KP, j, base + half < npix);
+  for (int it = 0; base < npix; base += stride, ++it) {
+    const long long pix = base + half;
+    const bool valid = pix < npix;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    {
+      const long long nb = base + stride + half;
+      ac::prefetch_row<M>(abuf + ((it + 1) & 1) * KP, a.Astate + (nb < npix ? nb : 0) * KP, j, nb < npix);
     }
-    float vmax = cv;
+    // shortlist of this pixel: the largest tensor-core value over the entries
+    float vmax = -INFINITY;
+    for (int c = j; c < ncand; c += 16)
+      if (valid) vmax = fmaxf(vmax, a.cand_val[pix * ncand + c]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-    int best_i;
+    for (int off = 8; off > 0; off >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    float bv = -INFINITY;
+    int bi = 0x7fffffff;
     if (a.mode != 0) {
       // precision study: the tensor-core value decides (ties -> lowest index)
-      int bi = (cv == vmax) ? ci : 0x7fffffff;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, off));
-      best_i = bi;
+      for (int c = j; c < ncand; c += 16)
+        if (valid && a.cand_val[pix * ncand + c] == vmax) bi = min(bi, a.cand_idx[pix * ncand + c]);
+      bv = vmax;
     } else {
       // |R~ - R| <= sum_k (|da_k||B| + |a_k||dB|) + accumulation <= 2^-9 sum|a~| (F16
       // operands, |B| <= 2) + 225 * 2^-23 * 2 sum|a~| + subnormal flush of a~ (2^-25 each)
-      const float E = 2.05e-3f * a.l1[pix] + 2e-5f;
+      const float E = valid ? 2.05e-3f * a.l1[pix] + 2e-5f : 0.f;
       const float thr = vmax - 2.f * E;
       // a group whose last entry is inside the window may hide further candidates
-      const bool ovf_lane = (lane < ncand) && ((lane % og) == og - 1) && (cv >= thr);
-      const bool overflow = __any_sync(0xffffffffu, ovf_lane);
-      // Q sums of the pixel (exact FP32 state)
-      const float* A = a.Astate + pix * a.kpad;
-      for (int e = lane; e < (K + 1) * K; e += 32) {
-        const int kx = e / K, ky = e % K + 1;
-        float sr, dr, si, di;
-        if (kx == 0) {
-          sr = 2.f * A[ky]; dr = 0.f; si = 0.f; di = 2.f * A[nh + ky];
+      bool ovf = false;
+      for (int c = j; c < ncand; c += 16)
+        if (valid && (c % og) == og - 1 && a.cand_val[pix * ncand + c] >= thr) ovf = true;
+      const bool overflow = ((__ballot_sync(0xffffffffu, ovf) >> (16 * half)) & 0xffffu) != 0;
+      if (valid) ac::build_qsums<M, QIT>(abuf + (it & 1) * KP, qbuf, qoff, j);
+      __syncwarp();
+      if (valid) {
+        if (!overflow) {
+          for (int c = j; c < ncand; c += 16) {
+            const float cv = a.cand_val[pix * ncand + c];
+            const int ci = a.cand_idx[pix * ncand + c];
+            if (cv >= thr && ci >= 0 && ci < L * L) {
+              const float r = ac::exact_R<M>(qbuf, tabx, L, ci);
+              if (r > bv || (r == bv && ci < bi)) { bv = r; bi = ci; }
+            }
+          }
         } else {
-          const int hp = K + (kx - 1) * M + (ky + K) + 1, hm = K + (kx - 1) * M + (-ky + K) + 1;
-          const float rp = A[hp], rm = A[hm], ip = A[nh + hp], im = A[nh + hm];
-          sr = rp + rm; dr = rp - rm; si = ip + im; di = ip - im;
-        }
-        qbuf[4 * e + 0] = sr; qbuf[4 * e + 1] = dr; qbuf[4 * e + 2] = si; qbuf[4 * e + 3] = di;
-      }
-      if (lane <= K) {
-        float qr, qi;
-        if (lane == 0) { qr = A[0]; qi = 0.f; }
-        else { const int h0 = K + (lane - 1) * M + K + 1; qr = A[h0]; qi = A[nh + h0]; }
-        qbuf[4 * (K + 1) * K + 2 * lane] = qr;
-        qbuf[4 * (K + 1) * K + 2 * lane + 1] = qi;
-      }
-      __syncwarp();
-      float bv = -INFINITY;
-      int bi = 0x7fffffff;
-      if (!overflow) {
-        if (lane < ncand && cv >= thr && ci < L * L) {
-          bv = exact_R<M>(qbuf, tabx, L, ci);
-          bi = ci;
-        }
-      } else {
-        if (lane == 0 && a.n_fallback) atomicAdd(a.n_fallback, 1);
-        for (int g = lane; g < L * L; g += 32) {
-          const float r = exact_R<M>(qbuf, tabx, L, g);
-          if (r > bv) { bv = r; bi = g; }
+          if (j == 0 && a.n_fallback) atomicAdd(a.n_fallback, 1);
+          for (int g = j; g < L * L; g += 16) {
+            const float r = ac::exact_R<M>(qbuf, tabx, L, g);
+            if (r > bv) { bv = r; bi = g; }       // g increases in this lane: first of equals kept
+          }
         }
       }
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ob > bv || (ob == bv && oi < bi)) { bv = ob; bi = oi; }
-      }
-      best_i = bi;
-      __syncwarp();
+    for (int off = 8; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > bv || (ob == bv && oi < bi)) { bv = ob; bi = oi; }
     }
-    if (lane == 0) {
-      const int b = (best_i >= 0 && best_i < L * L) ? best_i : 0;
+    if (valid && j == 0) {
+      const int b = (bi >= 0 && bi < L * L) ? bi : 0;
+      const int iy = int((float(b) + 0.5f) * invL), ix = b - iy * L;   // exact: b < 31^2
       a.vidx[pix] = b;
-      a.vx[pix] = -a.vmax + (b % L) * a.vstep;
-      a.vy[pix] = -a.vmax + (b / L) * a.vstep;
+      a.vx[pix] = -a.vmax + ix * a.vstep;
+      a.vy[pix] = -a.vmax + iy * a.vstep;
     }
+    __syncwarp();
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <int M>
@@ -219,12 +186,16 @@ cudaError_t launch_conv_m(const AutocorrTcArgs& a, cudaStream_t st) {
 
 template <int M>
 cudaError_t launch_rerank_m(const AutocorrTcArgs& a, cudaStream_t st) {
-  constexpr int K = (M - 1) / 2;
-  constexpr int QN = (4 * (K + 1) * K + 2 * (K + 1) + 3) & ~3;
-  const size_t smem = sizeof(float2) * size_t((a.L * (K + 1) + 1) & ~1) + sizeof(float) * kWarpsR * QN;
+  using G = ac::Geo<M>;
+  constexpr int K = G::K;
+  if (a.kpad != G::KP) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * size_t(kWarpsR) * 2 * (2 * G::KP + G::QN) +
+                      sizeof(float2) * size_t(a.L) * (K + 1);
   const long long npix = (long long)a.H * a.W;
-  long long blocks = (npix + kWarpsR - 1) / kWarpsR;
+  long long blocks = (npix + 2 * kWarpsR - 1) / (2 * kWarpsR);
   if (blocks > 148LL * 8) blocks = 148LL * 8;
+  cudaError_t e = cudaFuncSetAttribute(ac_rerank_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
   ac_rerank_kernel<M><<<unsigned(blocks), kWarpsR * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
