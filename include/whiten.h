@@ -146,10 +146,10 @@ int wh_push_frame_async(wh_stream *s, const float *frame_host, float *whitened_h
 
 /*
  * Wait until every kernel and copy enqueued on the stream (including
- * asynchronous pushes) has finished.  Returns WH_ECUDA if a bounded
+ * asynchronous pushes) has finished.  Returns WH_ETIMEOUT if a bounded
  * device-side wait gave up since the last check (the frame's results are then
- * not valid).
- * Errors: WH_EINVAL (NULL), WH_ECUDA.
+ * not valid); the synchronising wh_read_* calls report it the same way.
+ * Errors: WH_EINVAL (NULL), WH_ETIMEOUT, WH_ECUDA.
  */
 int wh_stream_sync(wh_stream *s);
 
@@ -161,6 +161,22 @@ int wh_stream_sync(wh_stream *s);
  * Errors: WH_EINVAL (NULL, or an index never pushed), WH_ECUDA.
  */
 int wh_stream_query_frame(wh_stream *s, long long frame_index, int wait);
+
+/*
+ * Self-tests of the failure path (no fault, no hang).
+ * wh_selftest_wait_timeout: runs one kernel whose bounded device-side wait
+ * (the helper every waiting kernel of this library uses) waits for an
+ * mbarrier phase that never completes; it gives up after limit_us
+ * microseconds (1..1000000), records it in a device flag and returns.
+ * Returns WH_ETIMEOUT when the timeout was detected (the expected result);
+ * the CUDA context stays usable.
+ * wh_stream_selftest_status: writes code into the stream's device status word
+ * as a kernel whose wait gave up would; the next synchronising call reports
+ * WH_ETIMEOUT once (code 0 clears it).
+ * Errors: WH_EINVAL, WH_ENOMEM, WH_ECUDA.
+ */
+int wh_selftest_wait_timeout(int limit_us, void *cuda_stream);
+int wh_stream_selftest_status(wh_stream *s, int code);
 
 /*
  * Allocation-free variant of wh_push_frame.  The paper has no counterpart; it

@@ -579,6 +579,13 @@ int wh_push_frame_async(wh_stream* s, const float* frame_host, float* whitened_h
   return WH_OK;
 }
 
+int wh_stream_selftest_status(wh_stream* s, int code) {
+  if (!s || code < 0) return WH_EINVAL;
+  WH_CU(cudaMemcpyAsync(s->d_err, &code, sizeof(int), cudaMemcpyHostToDevice, s->st));
+  WH_CU(cudaStreamSynchronize(s->st));
+  return WH_OK;
+}
+
 int wh_stream_sync(wh_stream* s) {
   if (!s) return WH_EINVAL;
   WH_CU(cudaStreamSynchronize(s->st));
@@ -615,13 +622,14 @@ int wh_stream_query_frame(wh_stream* s, long long frame_index, int wait) {
 
 // After a synchronisation: the device status word is nonzero if a bounded
 // wait inside one of this stream's kernels gave up (the results of that frame
-// are not valid); reported once as WH_ECUDA.
+// are not valid); reported once as WH_ETIMEOUT.
 static int check_device_status(wh_stream* s) {
   int h = 0;
   WH_CU(cudaMemcpy(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h != 0) {
     cudaMemset(s->d_err, 0, sizeof(int));
-    return wh_cuda_fail(cudaErrorLaunchTimeout, "a device-side wait timed out");
+    std::snprintf(wh_error_buffer(), 512, "a bounded device-side wait gave up (code %d)", h);
+    return WH_ETIMEOUT;
   }
   return WH_OK;
 }
