@@ -60,6 +60,15 @@ def spectrum_rel_err(gpu, ref):
     return float(np.max(err / np.maximum(rms, 1e-30)))
 
 
+def spectrum_rel_err_rms(gpu, ref):
+    """RMS over pixels of the per-pixel RMS_k |gpu - ref| / RMS_k |ref|."""
+    g = gpu.reshape(gpu.shape[0], gpu.shape[1], -1)
+    r = ref.reshape(ref.shape[0], ref.shape[1], -1)
+    rms = np.sqrt(np.mean(np.abs(r) ** 2, axis=-1))
+    e = np.sqrt(np.mean(np.abs(g - r) ** 2, axis=-1)) / np.maximum(rms, 1e-30)
+    return float(np.sqrt(np.mean(e ** 2)))
+
+
 def velocity_report(gpu_idx, ref_idx, ref_rs_frames, L, first=1):
     """Fraction identical, max grid-step distance, and whether the mismatches
     at frames with stored R' are near ties of the oracle's R'.

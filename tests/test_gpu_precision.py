@@ -61,6 +61,7 @@ def test_precision_study_config3():
         same = [[], []]
         steps = 0
         werr = [0.0, 0.0]
+        wsq = [[], []]
         rms = float(np.sqrt(np.mean(fr.astype(np.float64) ** 2)))
         for (y, x), ref in refs.items():
             gi = vel[:, y, x].astype(np.int32)
@@ -74,22 +75,37 @@ def test_precision_study_config3():
             e = np.abs(white[:, y, x] - ref2["whitened"][:, 0, 0])
             werr[0] = max(werr[0], float(np.nanmax(e[o.mpz:half])) / rms)
             werr[1] = max(werr[1], float(np.nanmax(e[half:])) / rms)
+            wsq[0].append(e[o.mpz:half] ** 2)
+            wsq[1].append(e[half:] ** 2)
         report[name] = {
             "velocity_identical_first_half": float(np.mean(np.concatenate(same[0]))),
             "velocity_identical_second_half": float(np.mean(np.concatenate(same[1]))),
             "velocity_max_grid_steps": steps,
             "whitened_max_err_over_rms_first_half": werr[0],
             "whitened_max_err_over_rms_second_half": werr[1],
+            "whitened_rms_err_over_rms_first_half": float(np.sqrt(np.mean(np.concatenate(wsq[0])))) / rms,
+            "whitened_rms_err_over_rms_second_half": float(np.sqrt(np.mean(np.concatenate(wsq[1])))) / rms,
         }
-    # spectrum error on a crop (the spectrum does not depend on the engine)
-    crop = np.ascontiguousarray(fr[:40, 480:544, 600:680])
-    g = P.run_gpu(crop, M, MZ, VMAX, VSTEP, spec_frames=(39,), debug=True)
-    ref = o.run(crop, spec_frames=[39], spectrum=True, windowed=True)
-    report["spectrum_rel_err"] = P.spectrum_rel_err(g["spectrum"][39], ref["spectrum"][0])
-    report["windowed_spectrum_rel_err"] = P.spectrum_rel_err(g["windowed"][39], ref["windowed"][0])
+    # spectrum error on a crop over the whole sequence (the spectrum does not
+    # depend on the engine): max and RMS over pixels of the per-pixel relative
+    # error, early and at the last frame (the deadbeat observer does not drift)
+    crop = np.ascontiguousarray(fr[:, 496:528, 620:660])
+    sf = (39, T - 1)
+    g = P.run_gpu(crop, M, MZ, VMAX, VSTEP, spec_frames=sf, debug=True)
+    ref = o.run(crop, spec_frames=list(sf), spectrum=True, windowed=True)
+    for n, t in enumerate(sf):
+        tag = "early" if n == 0 else "last"
+        report[f"spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][n])
+        report[f"spectrum_rel_err_rms_{tag}"] = P.spectrum_rel_err_rms(g["spectrum"][t], ref["spectrum"][n])
+        report[f"windowed_spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["windowed"][t], ref["windowed"][n])
+    report["spectrum_rel_err"] = max(report["spectrum_rel_err_early"], report["spectrum_rel_err_last"])
     report["frames"] = T
     report["sampled_pixels"] = len(pts)
     print("\n[precision] " + json.dumps(report), flush=True)
+    out = os.environ.get("WH_PREC_REPORT")
+    if out:
+        with open(out, "w") as f:
+            json.dump(report, f, indent=1)
     for name in ("fp32_exact_tc", "fp32_cuda_cores"):
         r = report[name]
         assert r["velocity_identical_first_half"] >= 0.999
