@@ -30,22 +30,26 @@ struct PefGeo {
   static constexpr int RT = kT + 2 * K;   // history tile edge
 };
 
-// One CTA per 16 x 16 output tile.  The history tile is kept as pairs of
-// consecutive rows, hp[m][r][x] = (x(r), x(r+1)), so one 8-byte load feeds a
-// packed FP32x2 FMA over the taps dy = 2i, 2i+1 of the y-sum; the x-weights of
-// the pixel's velocity come duplicated, (h, h), from the L1-cached table.
+// One CTA per 16 x 16 output tile, 128 threads: thread (tx2, ty) filters the
+// two pixels (2 tx2, ty) and (2 tx2 + 1, ty).  The history tile is kept as
+// pairs of consecutive rows, hp[m][r][x] = (x(r), x(r+1)), so one 8-byte value
+// feeds a packed FP32x2 FMA over the taps dy = 2i, 2i+1 of the y-sum, and one
+// 16-byte load of two adjacent columns serves both pixels (the second pixel's
+// window is the first's shifted by one column).  The x-weights of each pixel's
+// velocity come duplicated, (h, h), from the L1-cached table.
 template <int M, int MZ>
-__global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
+__global__ void __launch_bounds__(kT * kT / 2) pef_kernel(const PefArgs a) {
   constexpr int K = PefGeo<M>::K, RT = PefGeo<M>::RT;
   constexpr int J = (MZ - 1) / 2;
   constexpr bool EVEN = (MZ % 2) == 0;
+  constexpr int NQ = (M + 2) / 2;            // 16-byte column pairs covering M + 1 columns
   const int L = a.L, H = a.H, W = a.W;
   const int x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* hp = reinterpret_cast<float2*>(smem_raw);        // [MZ][RT][RT]
   float* cs = reinterpret_cast<float*>(hp + MZ * RT * RT);  // [J+1][MZ] cos, then sin
   float* sn = cs + (J + 1) * MZ;
-  const int tid = threadIdx.y * kT + threadIdx.x, nthr = kT * kT;
+  const int tid = threadIdx.y * (kT / 2) + threadIdx.x, nthr = kT * kT / 2;
   for (int i = tid; i < (J + 1) * MZ; i += nthr) {
     const int j = i / MZ, m = i % MZ;
     float s, c;
@@ -78,37 +82,63 @@ __global__ void __launch_bounds__(kT * kT) pef_kernel(const PefArgs a) {
     }
   }
   __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = 2 * threadIdx.x, ty = threadIdx.y;
   const int px = x0 + tx, py = y0 + ty;
   if (px >= W || py >= H) return;
+  const bool has_b = px + 1 < W;
   const size_t pix = size_t(py) * W + px;
-  int g = a.vidx[pix];
-  g = g < 0 ? 0 : (g >= L * L ? L * L - 1 : g);   // never index the tables out of range
-  const int gx = g % L, gy = g / L;
-  const float2* hw2 = reinterpret_cast<const float2*>(a.hw + pef_hw2_offset(L, MZ, M)) + size_t(gx) * MZ * M;
-  const float2* hwp = reinterpret_cast<const float2*>(a.hw + pef_hwp_offset(L, MZ, M)) + size_t(gy) * MZ * K;
-  const float* hwy = a.hw + size_t(gy) * MZ * M;
-  float Ihat = 0.f;
-#pragma unroll
+  // grid indices of the two pixels, clamped before they index any table
+  int ga = a.vidx[pix], gb = has_b ? a.vidx[pix + 1] : ga;
+  ga = ga < 0 ? 0 : (ga >= L * L ? L * L - 1 : ga);
+  gb = gb < 0 ? 0 : (gb >= L * L ? L * L - 1 : gb);
+  const float2* hw2 = reinterpret_cast<const float2*>(a.hw + pef_hw2_offset(L, MZ, M));
+  const float2* hwp = reinterpret_cast<const float2*>(a.hw + pef_hwp_offset(L, MZ, M));
+  const int gxa = ga % L, gya = ga / L, gxb = gb % L, gyb = gb / L;
+  float Ia = 0.f, Ib = 0.f;
+#pragma unroll 1
   for (int m = 0; m < MZ; ++m) {
-    float2 wx[M];
+    float2 wa[M], wb[M];
 #pragma unroll
-    for (int dx = 0; dx < M; ++dx) wx[dx] = __ldg(hw2 + m * M + dx);
-    const float2* hb = hp + (m * RT + ty) * RT + tx;
-    float2 acc = make_float2(0.f, 0.f);              // (even dy, odd dy) partial sums
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      float2 r = make_float2(0.f, 0.f);              // x-sums of rows dy = 2i, 2i+1
-#pragma unroll
-      for (int dx = 0; dx < M; ++dx) r = __ffma2_rn(wx[dx], hb[(2 * i) * RT + dx], r);
-      acc = __ffma2_rn(__ldg(hwp + m * K + i), r, acc);
+    for (int dx = 0; dx < M; ++dx) {
+      wa[dx] = __ldg(hw2 + (size_t(gxa) * MZ + m) * M + dx);
+      wb[dx] = __ldg(hw2 + (size_t(gxb) * MZ + m) * M + dx);
     }
-    float rl = 0.f;                                   // last row dy = 2K
+    const float4* hb = reinterpret_cast<const float4*>(hp + (m * RT + ty) * RT + tx);
+    float2 acca = make_float2(0.f, 0.f), accb = make_float2(0.f, 0.f);   // (even dy, odd dy)
+    float rla = 0.f, rlb = 0.f;
 #pragma unroll
-    for (int dx = 0; dx < M; ++dx) rl = fmaf(wx[dx].x, hb[(2 * K) * RT + dx].x, rl);
-    Ihat += fmaf(__ldg(hwy + m * M + 2 * K), rl, acc.x + acc.y);
+    for (int i = 0; i <= K; ++i) {
+      // row pair (2i, 2i+1) (i < K), or the last row 2K in .x (i == K); columns tx .. tx+M
+      float2 d[2 * NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 v = hb[(2 * i) * (RT / 2) + q];
+        d[2 * q] = make_float2(v.x, v.y);
+        d[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      if (i < K) {
+        float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int dx = 0; dx < M; ++dx) {
+          ra = __ffma2_rn(wa[dx], d[dx], ra);
+          rb = __ffma2_rn(wb[dx], d[dx + 1], rb);
+        }
+        acca = __ffma2_rn(__ldg(hwp + (size_t(gya) * MZ + m) * K + i), ra, acca);
+        accb = __ffma2_rn(__ldg(hwp + (size_t(gyb) * MZ + m) * K + i), rb, accb);
+      } else {
+#pragma unroll
+        for (int dx = 0; dx < M; ++dx) {
+          rla = fmaf(wa[dx].x, d[dx].x, rla);
+          rlb = fmaf(wb[dx].x, d[dx + 1].x, rlb);
+        }
+      }
+    }
+    Ia += fmaf(__ldg(a.hw + (size_t(gya) * MZ + m) * M + 2 * K), rla, acca.x + acca.y);
+    Ib += fmaf(__ldg(a.hw + (size_t(gyb) * MZ + m) * M + 2 * K), rlb, accb.x + accb.y);
   }
-  a.whitened[pix] = hp[(a.mpz * RT + ty + K) * RT + tx + K].x - Ihat;
+  const float2 c = hp[(a.mpz * RT + ty + K) * RT + tx + K];   // (x(row), x(row+1)): need row's two columns
+  a.whitened[pix] = c.x - Ia;
+  if (has_b) a.whitened[pix + 1] = hp[(a.mpz * RT + ty + K) * RT + tx + K + 1].x - Ib;
 }
 
 // Raw spectrum S(k; n) of Eq. (6)-(7) from the observer state, by direct
@@ -159,7 +189,7 @@ static cudaError_t launch_pef_t(const PefArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(pef_kernel<M, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   dim3 grid((a.W + kT - 1) / kT, (a.H + kT - 1) / kT);
-  pef_kernel<M, MZ><<<grid, dim3(kT, kT), smem, st>>>(a);
+  pef_kernel<M, MZ><<<grid, dim3(kT / 2, kT), smem, st>>>(a);
   return cudaGetLastError();
 }
 
