@@ -162,6 +162,32 @@ int wh_stream_sync(wh_stream *s);
  */
 int wh_stream_query_frame(wh_stream *s, long long frame_index, int wait);
 
+/* One detection of the threshold detector. */
+typedef struct {
+  int y, x;      /* pixel: row, column */
+  float value;   /* whitened value E at the pixel */
+  float vx, vy;  /* velocity (pixels/frame) that tuned the prediction-error filter there */
+} wh_detection;
+
+/*
+ * Threshold detector on the latest whitened frame (the point-target detection
+ * that the whitening prepares, Sec. 1; the paper's detector and tracker are
+ * not specified further, the tracker is not part of this library): every
+ * pixel with E >= k_sigma * sigma, sigma = RMS of E over the frame, in raster
+ * order (row, then column), with the velocity of the same push (the one
+ * used by the PEF that produced E).
+ *   k_sigma     threshold in units of sigma (> 0)
+ *   max_det     capacity of out; at most max_det entries are written
+ *   out         wh_detection[max_det], device (is_device = 1) or host memory
+ *   n_out       receives the number of pixels above the threshold (may exceed max_det)
+ *   sigma_out   NULL or receives sigma
+ *   frame_index NULL or receives the index of the whitened frame (t - delay_z)
+ * Synchronises the stream.  Deterministic (fixed-order reductions).
+ * Errors: WH_EINVAL, WH_ENOTREADY (fewer than delay_z + 1 frames), WH_ENOMEM, WH_ECUDA.
+ */
+int wh_detect(wh_stream *s, float k_sigma, int max_det, wh_detection *out, int *n_out,
+              float *sigma_out, int is_device, long long *frame_index);
+
 /*
  * Self-tests of the failure path (no fault, no hang).
  * wh_selftest_wait_timeout: runs one kernel whose bounded device-side wait

@@ -63,6 +63,8 @@ _SIGS = {
     "wh_push_frame_noalloc": (C.c_int, [_VP, _VP, C.c_int]),
     "wh_push_frame_async": (C.c_int, [_VP, _VP, _VP, _VP, _VP, C.POINTER(C.c_longlong)]),
     "wh_stream_sync": (C.c_int, [_VP]),
+    "wh_detect": (C.c_int, [_VP, C.c_float, C.c_int, _VP, C.POINTER(C.c_int), C.POINTER(C.c_float),
+                            C.c_int, C.POINTER(C.c_longlong)]),
     "wh_selftest_wait_timeout": (C.c_int, [C.c_int, _VP]),
     "wh_stream_selftest_status": (C.c_int, [_VP, C.c_int]),
     "wh_stream_query_frame": (C.c_int, [_VP, C.c_longlong, C.c_int]),

@@ -207,7 +207,7 @@ static void free_stream(wh_stream* s) {
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
                   s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
                   s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather, s->d_ymlp,
-                  s->d_list, s->d_nlist, s->d_nfb_total};
+                  s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -266,6 +266,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->d_ymlp = nullptr; s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
   s->mlp_frames = 0;
   s->as = nullptr;
+  s->d_det = nullptr; s->det_bytes = 0; s->d_det_list = nullptr; s->det_list_cap = 0;
   s->tc_mode = pmode == 0 ? 0 : 1;
   s->tc_bf16 = pmode == 2 ? 1 : 0;
   s->use_tc = (pmode != 0) || ((p.precision & WH_PREC_TC_SHORTLIST) && autocorr_tc_supported(M));

@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "../../include/whiten.h"
 #include "common.cuh"
 
 struct wh_stream {
@@ -65,6 +66,11 @@ struct wh_stream {
     int par;                   // set of the next push
   };
   Async* as;
+  // threshold detector scratch (wh_detect)
+  void* d_det;
+  size_t det_bytes;
+  wh_detection* d_det_list;
+  int det_list_cap;
   // per-kernel timing (wh_profile_enable)
   int prof;
   std::vector<cudaEvent_t> ev;   // 4 per timed frame

@@ -123,6 +123,22 @@ class WhitenStream:
               "wh_push_frame_async")
         return int(idx.value)
 
+    DETECTION_DTYPE = np.dtype([("y", np.int32), ("x", np.int32), ("value", np.float32),
+                                ("vx", np.float32), ("vy", np.float32)])
+
+    def detect(self, k_sigma: float = 5.0, max_det: int = 4096):
+        """Threshold detector on the latest whitened frame (wh_detect).
+
+        Returns (detections, n_total, sigma, frame_index); detections is a
+        structured array (y, x, value, vx, vy) in raster order, at most max_det
+        long, n_total the number of pixels above k_sigma * sigma."""
+        out = np.zeros(max(max_det, 0), dtype=self.DETECTION_DTYPE)
+        n, sig, idx = C.c_int(), C.c_float(), C.c_longlong()
+        check(self.lib.wh_detect(self._s, C.c_float(k_sigma), int(max_det),
+                                 C.c_void_p(out.ctypes.data if max_det > 0 else 0), C.byref(n),
+                                 C.byref(sig), 0, C.byref(idx)), "wh_detect")
+        return out[:min(n.value, max_det)], n.value, sig.value, idx.value
+
     def wait_frame(self, index: int) -> None:
         check(self.lib.wh_stream_query_frame(self._s, C.c_longlong(index), 1), "wh_stream_query_frame")
 

@@ -51,11 +51,13 @@ def run_gpu(frames, M, Mz, vmax, step, spec_frames=(), debug=False, **kw):
     return out
 
 
-def spectrum_rel_err(gpu, ref):
-    """Per-pixel max_k |gpu - ref| / RMS_k |ref| (max over pixels)."""
+def spectrum_rel_err(gpu, ref, scale_ref=None):
+    """Per-pixel max_k |gpu - ref| / RMS_k |ref| (max over pixels); with
+    scale_ref, the RMS is taken of that array instead (same shape)."""
     g = gpu.reshape(gpu.shape[0], gpu.shape[1], -1)
     r = ref.reshape(ref.shape[0], ref.shape[1], -1)
-    rms = np.sqrt(np.mean(np.abs(r) ** 2, axis=-1))
+    sr = r if scale_ref is None else scale_ref.reshape(ref.shape[0], ref.shape[1], -1)
+    rms = np.sqrt(np.mean(np.abs(sr) ** 2, axis=-1))
     err = np.max(np.abs(g - r), axis=-1)
     return float(np.max(err / np.maximum(rms, 1e-30)))
 

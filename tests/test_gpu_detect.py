@@ -1,0 +1,35 @@
+"""Threshold detector on the whitened output (needs a B300): the same pixels,
+values and velocity tags as thresholding the read-back frame on the host."""
+import numpy as np
+import pytest
+
+from paper_1408_3526_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def test_detector_matches_host_threshold():
+    from paper_1408_3526_b300.stream import WhitenStream
+    sc = scenes.config1_scene(T=24, H=64, W=64, seed=1)
+    with WhitenStream(64, 64, 9, 4, 2.0, 0.25) as s:
+        for t in range(sc.frames.shape[0]):
+            s.push(np.ascontiguousarray(sc.frames[t]))
+        e, fi = s.read_whitened()
+        vx, vy, _, ti = s.read_velocity()
+        det, n, sigma, di = s.detect(k_sigma=4.0, max_det=1024)
+        assert di == fi
+        ref_sigma = float(np.sqrt(np.mean(e.astype(np.float64) ** 2)))
+        assert abs(sigma - ref_sigma) <= 1e-5 * ref_sigma
+        ys, xs = np.nonzero(e >= np.float32(4.0) * np.float32(sigma))
+        assert n == len(ys)
+        assert np.array_equal(det["y"], ys) and np.array_equal(det["x"], xs)     # raster order
+        assert np.array_equal(det["value"], e[ys, xs])
+        assert np.array_equal(det["vx"], vx[ys, xs]) and np.array_equal(det["vy"], vy[ys, xs])
+        # capacity smaller than the count: the first entries in raster order
+        det2, n2, _, _ = s.detect(k_sigma=4.0, max_det=1)
+        assert n2 == n and len(det2) == min(1, n)
+        if n:
+            assert det2[0]["y"] == ys[0] and det2[0]["x"] == xs[0]
+        # count only
+        _, n3, _, _ = s.detect(k_sigma=4.0, max_det=0)
+        assert n3 == n

@@ -14,7 +14,8 @@ from tests import _parity as P
 pytestmark = pytest.mark.gpu
 
 
-def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=True, **kw):
+def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=True,
+             win_tol=P.SPEC_TOL, **kw):
     T, H, W = frames.shape
     g = P.run_gpu(frames, M, Mz, vmax, step, spec_frames=spec_frames, debug=debug, **kw)
     kw = dict(kw)
@@ -23,11 +24,13 @@ def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=
     kw.pop("precision", None)
     ref = o.run(frames, spec_frames=list(spec_frames), spectrum=True, power=debug,
                 autocorr=True, windowed=debug)
-    m = {"spec": 0.0, "win": 0.0, "pow": 0.0, "rs": 0.0}
+    m = {"spec": 0.0, "win": 0.0, "win_raw": 0.0, "pow": 0.0, "rs": 0.0}
     for i, t in enumerate(spec_frames):
         m["spec"] = max(m["spec"], P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][i]))
         if debug:
             m["win"] = max(m["win"], P.spectrum_rel_err(g["windowed"][t], ref["windowed"][i]))
+            m["win_raw"] = max(m["win_raw"], P.spectrum_rel_err(g["windowed"][t], ref["windowed"][i],
+                                                                 scale_ref=ref["spectrum"][i]))
             m["pow"] = max(m["pow"], P.spectrum_rel_err(g["power"][t], ref["power"][i]))
         ar = ref["autocorr"][i]
         scale = np.abs(ar).reshape(H, W, -1).max(-1)[..., None, None]
@@ -37,10 +40,11 @@ def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=
     ref2 = o.run(frames, vel_override=g["vel_index"], velocity=False)
     err = P.whitened_err(g["whitened"], ref2["whitened"], frames, o.mpz)
     print(f"\n[parity M={M} Mz={Mz} {T}x{H}x{W}] spec {m['spec']:.2e} windowed {m['win']:.2e} "
+          f"(vs raw RMS {m['win_raw']:.2e}) "
           f"power {m['pow']:.2e} R' {m['rs']:.2e} vel_same {frac:.5f} max_steps {steps} "
           f"tie {tie:.2e} whitened {err:.2e} xRMS mismatches {bad[:6]}", flush=True)
     assert m["spec"] <= P.SPEC_TOL
-    assert m["win"] <= P.SPEC_TOL
+    assert m["win"] <= win_tol
     assert m["pow"] <= 2 * P.SPEC_TOL
     assert m["rs"] <= P.SPEC_TOL
     if check_vel_frac:
@@ -49,6 +53,18 @@ def _compare(frames, M, Mz, vmax, step, spec_frames, debug=True, check_vel_frac=
     assert tie <= P.TIE_TOL, (tie, bad)
     assert err <= P.WHITE_TOL_REL, err
     return g, ref
+
+
+def test_parity_paper_simulation():
+    """The paper's own simulation recipe (Sec. 3) as a second regression
+    workload: 25 sinusoids translating between grid points, an occluding
+    truncated target, 64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2/4."""
+    sc = scenes.paper_sim_scene(T=32)
+    # Its clutter energy sits mostly in the DC bin that the high-pass removes,
+    # so the windowed bins are small next to the raw-scale FP32 sums they come
+    # from: the windowed spectrum is held to 2e-4 of its own RMS here (the raw
+    # spectrum keeps 1e-4; the error against the raw spectrum's RMS is printed).
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), win_tol=2 * P.SPEC_TOL)
 
 
 @pytest.mark.parametrize("precision", [16, 0], ids=["tc_shortlist_rerank", "cuda_cores"])
