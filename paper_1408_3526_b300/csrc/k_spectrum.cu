@@ -48,6 +48,7 @@ namespace wh {
 namespace {
 
 constexpr int kZN = kMaxMz - 2;     // temporal orders Mz = 3 .. kMaxMz
+constexpr int kSegRows = 256;       // longest run of the y-recursion (output rows)
 
 // Resonator twiddles w_k = e^{+j2pi ky/M} and centring phases c_k =
 // e^{-j2pi ky K/M} (k = ky + K) per window size (index (M-3)/2), packed for
@@ -313,7 +314,10 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   for (long long u = u0; u < u1;) {
     const int strip = int(u / H);
     const int y0 = int(u % H);
-    const int y1 = int(min((long long)H, (long long)y0 + (u1 - u)));
+    // at most kSegRows output rows per recursion: the y-SDFT restarts from zero
+    // (with its 2K-row warm-up) so rounding that the comb/resonator pole-zero
+    // cancellation leaves behind cannot accumulate along an arbitrarily long column
+    const int y1 = int(min(min((long long)H, (long long)y0 + (u1 - u)), (long long)y0 + kSegRows));
     u += y1 - y0;
     const int x0 = strip * TW;
     const int nrows = y1 - y0 + 2 * K;
