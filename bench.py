@@ -56,7 +56,7 @@ assert sum(KERNEL_BYTES_PER_PX.values()) == BYTES_PER_PX
 # while those sources are unchanged)
 PROFILE_OF = {
     "spectrum": ("profiles/spectrum_512x640_m15_mz6.md", ["k_spectrum.cu", "common.cuh"]),
-    "autocorr_argmax": ("profiles/autocorr_512x640_m15.md", ["k_autocorr.cu", "common.cuh"]),
+    "autocorr_argmax": ("profiles/autocorr_512x640_m15.md", ["k_autocorr.cu", "ac_common.cuh", "common.cuh"]),
     "pef": ("profiles/pef_512x640_m15_mz6.md", ["k_pef.cu", "common.cuh"]),
 }
 
