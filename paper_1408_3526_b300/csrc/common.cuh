@@ -148,6 +148,17 @@ __host__ __device__ constexpr int spec_tile_w(int M, int Mz) {
   return tw;
 }
 
+// Resident blocks per SM (and the SM count) of a kernel at a block size and
+// dynamic shared-memory size, with that shared-memory size allowed on the
+// kernel; the result is cached per (kernel, device, threads, smem), so the
+// attribute call and the occupancy query run once rather than every frame.
+struct ResidentShape { int nsm, per_sm; };
+cudaError_t resident_shape_of(const void* kernel, int threads, size_t smem, ResidentShape* out);
+template <typename F>
+inline cudaError_t resident_shape(F* kernel, int threads, size_t smem, ResidentShape* out) {
+  return resident_shape_of(reinterpret_cast<const void*>(kernel), threads, smem, out);
+}
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st);

@@ -166,16 +166,12 @@ cudaError_t launch_mp(const AutocorrArgs& a, cudaStream_t st) {
                       sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * LP;
   const long long npix = (long long)a.H * a.W;
   auto kern = a.rs_out ? autocorr_kernel<M, true, LP> : autocorr_kernel<M, false, LP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   // one resident wave (blocks per SM from the occupancy of this shape), the
   // pixel pairs strided over it, so no partial last wave idles SMs
-  int dev = 0, nsm = 148, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+  ResidentShape rs{};
+  cudaError_t e = resident_shape(kern, kWarps * 32, smem, &rs);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  const int nsm = rs.nsm, per_sm = rs.per_sm < 1 ? 1 : rs.per_sm;
   long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
   if (blocks > (long long)nsm * per_sm) blocks = (long long)nsm * per_sm;
   kern<<<unsigned(blocks), kWarps * 32, smem, st>>>(a);

@@ -192,14 +192,10 @@ cudaError_t launch_rerank_m(const AutocorrTcArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(float) * size_t(kWarpsR) * 2 * (2 * G::KP + G::QN) +
                       sizeof(float2) * size_t(a.L) * (K + 1);
   const long long npix = (long long)a.H * a.W;
-  cudaError_t e = cudaFuncSetAttribute(ac_rerank_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  ResidentShape rs{};
+  cudaError_t e = resident_shape(ac_rerank_kernel<M>, kWarpsR * 32, smem, &rs);
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 148, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ac_rerank_kernel<M>, kWarpsR * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  const int nsm = rs.nsm, per_sm = rs.per_sm < 1 ? 1 : rs.per_sm;
   long long blocks = (npix + 2 * kWarpsR - 1) / (2 * kWarpsR);
   if (blocks > (long long)nsm * per_sm) blocks = (long long)nsm * per_sm;
   ac_rerank_kernel<M><<<unsigned(blocks), kWarpsR * 32, smem, st>>>(a);

@@ -186,7 +186,8 @@ template <int M, int MZ>
 static cudaError_t launch_pef_t(const PefArgs& a, cudaStream_t st) {
   constexpr int RT = PefGeo<M>::RT, J = (MZ - 1) / 2;
   const size_t smem = sizeof(float2) * size_t(MZ) * RT * RT + sizeof(float) * 2 * size_t(J + 1) * MZ;
-  cudaError_t e = cudaFuncSetAttribute(pef_kernel<M, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  ResidentShape rs{};
+  cudaError_t e = resident_shape(pef_kernel<M, MZ>, kT * kT / 2, smem, &rs);   // sets the smem attribute once
   if (e != cudaSuccess) return e;
   dim3 grid((a.W + kT - 1) / kT, (a.H + kT - 1) / kT);
   pef_kernel<M, MZ><<<grid, dim3(kT / 2, kT), smem, st>>>(a);

@@ -635,13 +635,10 @@ cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   if (a.tw != G::TW || a.kpad != G::KPAD) return cudaErrorInvalidValue;
   const bool dump = a.dump_win != nullptr;
   auto kern = dump ? spectrum_kernel<M, MZ, true> : spectrum_kernel<M, MZ, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM));
+  ResidentShape rs{};
+  cudaError_t e = resident_shape(kern, G::NTHR, G::SMEM, &rs);
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 148, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::NTHR, G::SMEM);
-  if (e != cudaSuccess) return e;
+  const int nsm = rs.nsm, per_sm = rs.per_sm;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // one wave of CTAs, each with an equal share of the (strip, row) units
   const long long units = (long long)((a.W + G::TW - 1) / G::TW) * a.H;
