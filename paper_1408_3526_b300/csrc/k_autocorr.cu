@@ -49,7 +49,10 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
   float* abuf = sbase + hw * 2 * KP;                                                    // [2][KP]
   float* qbuf = sbase + kWarps * 2 * 2 * KP + hw * QN;                                  // [QN]
   constexpr int Lp = LP;          // row stride (>= L, even: rows gy, gy+1 load as one float4)
-  float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * (K + 1) * Lp;   // [K+1][Lp]
+  // per half-warp T buffer, padded by 64 bytes so the two half-warps' broadcast
+  // loads fall in different shared-memory banks
+  constexpr int TS = (K + 1) * Lp + 8;
+  float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * TS;   // [K+1][Lp]
   // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
   float2 cs[K];
   const bool act = j < Lh;
@@ -163,7 +166,7 @@ template <int M, int LP>
 cudaError_t launch_mp(const AutocorrArgs& a, cudaStream_t st) {
   constexpr int K = (M - 1) / 2;
   const size_t smem = sizeof(float) * size_t(kWarps) * 2 * (2 * AcSmem<M>::kPad + AcSmem<M>::kQ) +
-                      sizeof(float2) * size_t(kWarps) * 2 * (K + 1) * LP;
+                      sizeof(float2) * size_t(kWarps) * 2 * ((K + 1) * LP + 8);
   const long long npix = (long long)a.H * a.W;
   auto kern = a.rs_out ? autocorr_kernel<M, true, LP> : autocorr_kernel<M, false, LP>;
   // one resident wave (blocks per SM from the occupancy of this shape), the
