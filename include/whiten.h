@@ -80,9 +80,17 @@ typedef struct {
     int    band;        /* B, PEF spatial half-bandwidth (Eq. (2), W = 2B+1); <= 0: round(M/3) */
     int    delay_z;     /* m'_z, output delay in frames; < 0: floor((Mz-1)/2) */
     double alpha;       /* smoother pole (Sec. 2 after Eq. (10)); < 0: exp(-1/10) */
-    int    precision;   /* WH_PREC_* (bit-or WH_PREC_KAHAN) */
+    int    precision;   /* WH_PREC_* flags */
     int    debug_dump;  /* 1: keep the windowed spectrum and power of the last frame for
                            wh_read_spectrum (slow; tests only) */
+    int    pipeline;    /* 1: overlap consecutive frames: the spectrum kernel of frame t+1
+                           runs on an internal CUDA stream while the search and PEF of frame
+                           t run on a second one (the smoothed state is double-buffered,
+                           +kpad*4 bytes per pixel); results are identical to pipeline = 0.
+                           The work no longer runs on the caller's CUDA stream: the wh_read_*
+                           calls and wh_detect order themselves after it, and raw pointers
+                           from wh_output_pointers are valid after wh_stream_sync.
+                           Default 0. */
 } wh_params;
 
 typedef struct wh_stream wh_stream;   /* opaque */
@@ -152,6 +160,16 @@ int wh_push_frame_async(wh_stream *s, const float *frame_host, float *whitened_h
  * Errors: WH_EINVAL (NULL), WH_ETIMEOUT, WH_ECUDA.
  */
 int wh_stream_sync(wh_stream *s);
+
+/*
+ * Make the stream's CUDA stream (the one given at creation) wait, on the
+ * device, for every kernel enqueued so far: with wh_params.pipeline = 1 the
+ * kernels run on internal streams, and work the caller enqueues on its own
+ * stream after this call (events, copies, kernels) sees all of them.  No
+ * host synchronisation; a no-op without the pipeline.
+ * Errors: WH_EINVAL (NULL), WH_ECUDA.
+ */
+int wh_stream_join(wh_stream *s);
 
 /*
  * Whether the host outputs of frame frame_index (from wh_push_frame_async)

@@ -39,7 +39,7 @@ class wh_vgrid(C.Structure):
 
 class wh_params(C.Structure):
     _fields_ = [("band", C.c_int), ("delay_z", C.c_int), ("alpha", C.c_double),
-                ("precision", C.c_int), ("debug_dump", C.c_int)]
+                ("precision", C.c_int), ("debug_dump", C.c_int), ("pipeline", C.c_int)]
 
 
 class WhitenError(RuntimeError):
@@ -63,6 +63,7 @@ _SIGS = {
     "wh_push_frame_noalloc": (C.c_int, [_VP, _VP, C.c_int]),
     "wh_push_frame_async": (C.c_int, [_VP, _VP, _VP, _VP, _VP, C.POINTER(C.c_longlong)]),
     "wh_stream_sync": (C.c_int, [_VP]),
+    "wh_stream_join": (C.c_int, [_VP]),
     "wh_detect": (C.c_int, [_VP, C.c_float, C.c_int, _VP, C.POINTER(C.c_int), C.POINTER(C.c_float),
                             C.c_int, C.POINTER(C.c_longlong)]),
     "wh_selftest_wait_timeout": (C.c_int, [C.c_int, _VP]),

@@ -49,7 +49,8 @@ struct SpecArgs {
   const float* frame;
   const float* obs_old;
   float* obs_new;
-  float* Astate;
+  float* Astate;                // smoothed state of the previous frame (read)
+  float* Astate_out;            // where the updated state goes; nullptr: in place
   const SpecTables* tables;     // device copy
   const int* hgather;           // [nh+1][nslot] offsets (c*M + iy) into a pixel's P block
   float2* dump_win;             // optional [H*W][Mz][M][M]

@@ -115,6 +115,7 @@ extern "C" int wh_detect(wh_stream* s, float k_sigma, int max_det, wh_detection*
                          float* sigma_out, int is_device, long long* frame_index) {
   if (!s || max_det < 0 || (max_det > 0 && !out) || !n_out || !(k_sigma > 0.f)) return WH_EINVAL;
   if (s->t < s->mpz + 1) return WH_ENOTREADY;
+  { const int jr = wh_join_pipeline(s); if (jr != WH_OK) return jr; }
   const long long n = (long long)s->H * s->W;
   constexpr int kNB = 296;
   // scratch: partial sums, sigma/threshold, row counts and offsets, total, and

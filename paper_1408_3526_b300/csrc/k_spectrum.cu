@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     };
     auto store_row = [&](int r) {         // thread 0, after a CTA barrier
       const int b = row_slot(r);
-      float* dst = a.Astate + (size_t(y0 + r) * W + x0) * KPAD;
+      float* dst = (a.Astate_out ? a.Astate_out : a.Astate) + (size_t(y0 + r) * W + x0) * KPAD;
       asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                    ::"l"(dst), "r"(tc::smem_u32(srow + b * G::SROW)), "r"(row_bytes) : "memory");
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");

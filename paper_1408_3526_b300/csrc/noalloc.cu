@@ -102,6 +102,7 @@ __global__ void noalloc_table_kernel(uint16_t* table, int M, int L, float vmax, 
 
 extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_device) {
   if (!s || !frame) return WH_EINVAL;
+  if (s->pipeline) return WH_EUNSUP;          // runs on the caller's stream only
   if (s->M > 15 || s->L * s->L > kRows || !autocorr_tc_supported(s->M)) {
     std::snprintf(wh_error_buffer(), 512,
                   "wh_push_frame_noalloc: window %d / grid %dx%d beyond its limits (M <= 15, L <= 25)",

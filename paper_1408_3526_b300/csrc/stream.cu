@@ -199,9 +199,23 @@ static void free_async(wh_stream* s) {
   s->as = nullptr;
 }
 
+static void free_pipeline(wh_stream* s) {
+  if (!s->pipeline) return;
+  if (s->st_s) cudaStreamSynchronize(s->st_s);
+  if (s->st_p) cudaStreamSynchronize(s->st_p);
+  for (cudaEvent_t e : {s->ev_user, s->ev_spec, s->ev_join, s->ev_pef[0], s->ev_pef[1]})
+    if (e) cudaEventDestroy(e);
+  if (s->st_s) cudaStreamDestroy(s->st_s);
+  if (s->st_p) cudaStreamDestroy(s->st_p);
+  if (s->Astate_alt) cudaFree(s->Astate_alt);
+  s->st_s = s->st_p = nullptr;
+  s->Astate_alt = nullptr;
+}
+
 static void free_stream(wh_stream* s) {
   if (!s) return;
   free_async(s);
+  free_pipeline(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
@@ -224,6 +238,7 @@ int wh_default_params(int window, int temporal_order, wh_params* p) {
   p->alpha = std::exp(-0.1);
   p->precision = WH_PREC_FP32;
   p->debug_dump = 0;
+  p->pipeline = 0;
   return WH_OK;
 }
 
@@ -244,6 +259,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     if (opt->alpha >= 0) p.alpha = opt->alpha;
     p.precision = opt->precision;
     p.debug_dump = opt->debug_dump;
+    p.pipeline = opt->pipeline;
   }
   const int K = (M - 1) / 2;
   if (p.band > K || p.delay_z >= Mz || p.alpha >= 1.0) return WH_EINVAL;
@@ -289,6 +305,14 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   alloc((void**)&s->obs[0], sizeof(float) * npix * Mz);
   alloc((void**)&s->obs[1], sizeof(float) * npix * Mz);
   alloc((void**)&s->Astate, sizeof(float) * npix * s->kpad);
+  s->pipeline = p.pipeline ? 1 : 0;
+  if (s->pipeline) {
+    alloc((void**)&s->Astate_alt, sizeof(float) * npix * s->kpad);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&s->ev_user, &s->ev_spec, &s->ev_join, &s->ev_pef[0], &s->ev_pef[1]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  }
   alloc((void**)&s->frame, sizeof(float) * npix);
   alloc((void**)&s->whitened, sizeof(float) * npix);
   alloc((void**)&s->vx, sizeof(float) * npix);
@@ -431,9 +455,31 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   return WH_OK;
 }
 
+}  // extern "C"
+
+// Order the caller's stream after every frame-pipeline kernel enqueued so far.
+static int join_pipeline(wh_stream* s) { return wh_join_pipeline(s); }
+int wh_join_pipeline(wh_stream* s) {
+  if (!s->pipeline || !s->pipe_work) return WH_OK;
+  WH_CU(cudaEventRecord(s->ev_join, s->st_s));
+  WH_CU(cudaStreamWaitEvent(s->st, s->ev_join, 0));
+  WH_CU(cudaEventRecord(s->ev_join, s->st_p));
+  WH_CU(cudaStreamWaitEvent(s->st, s->ev_join, 0));
+  return WH_OK;
+}
+
+extern "C" {
+
 int wh_reset_stream(wh_stream* s) {
   if (!s) return WH_EINVAL;
   const size_t npix = size_t(s->H) * s->W;
+  if (s->pipeline) {
+    WH_CU(cudaStreamSynchronize(s->st_s));
+    WH_CU(cudaStreamSynchronize(s->st_p));
+    WH_CU(cudaMemsetAsync(s->Astate_alt, 0, sizeof(float) * npix * s->kpad, s->st));
+    s->pef_used[0] = s->pef_used[1] = 0;
+    s->pipe_work = 0;
+  }
   WH_CU(cudaMemsetAsync(s->obs[0], 0, sizeof(float) * npix * s->Mz, s->st));
   WH_CU(cudaMemsetAsync(s->obs[1], 0, sizeof(float) * npix * s->Mz, s->st));
   WH_CU(cudaMemsetAsync(s->Astate, 0, sizeof(float) * npix * s->kpad, s->st));
@@ -446,9 +492,20 @@ int wh_reset_stream(wh_stream* s) {
 
 static int check_device_status(wh_stream* s);
 
-// The three kernels of one frame on s->st, reading the device frame src and
-// writing s->whitened / s->vx / s->vy / s->vidx.
-static int push_kernels(wh_stream* s, const float* src) {
+// The three kernels of one frame, reading the device frame src and writing
+// s->whitened / s->vx / s->vy / s->vidx.  Without the frame pipeline all run on
+// s->st; with it the spectrum kernel runs on st_s (after the PEF of frame t-2,
+// whose observer and smoothed-state buffers it reuses) and the search and PEF
+// on st_p (after this frame's spectrum).  wait_spec / wait_search: optional
+// events the spectrum / the search must follow.
+static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = nullptr,
+                        cudaEvent_t wait_search = nullptr) {
+  const cudaStream_t user = s->st;
+  const cudaStream_t ss = s->pipeline ? s->st_s : s->st;
+  const cudaStream_t sp = s->pipeline ? s->st_p : s->st;
+  const int k = int(s->t & 1);
+  if (s->pipeline && s->pef_used[k]) WH_CU(cudaStreamWaitEvent(ss, s->ev_pef[k], 0));
+  if (wait_spec) WH_CU(cudaStreamWaitEvent(ss, wait_spec, 0));
   cudaEvent_t* ev = nullptr;
   if (s->prof && s->ev_used + 4 <= 4 * 65536) {
     while (s->ev.size() < s->ev_used + 4) {
@@ -459,34 +516,44 @@ static int push_kernels(wh_stream* s, const float* src) {
     ev = &s->ev[s->ev_used];
     s->ev_used += 4;
   }
-  if (ev) WH_CU(cudaEventRecord(ev[0], s->st));
+  if (ev) WH_CU(cudaEventRecord(ev[0], ss));
   SpecArgs sa{};
   sa.H = s->H; sa.W = s->W; sa.M = s->M; sa.Mz = s->Mz; sa.tw = s->tw; sa.th = s->th;
   sa.kpad = s->kpad; sa.alpha = float(s->alpha); sa.frame = src;
   sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
+  sa.Astate_out = s->pipeline ? s->Astate_alt : nullptr;
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
   sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
   sa.err = s->d_err;
-  cudaError_t e = launch_spectrum(sa, s->st);
+  cudaError_t e = launch_spectrum(sa, ss);
   if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
-  if (ev) WH_CU(cudaEventRecord(ev[1], s->st));
+  if (ev) WH_CU(cudaEventRecord(ev[1], ss));
+  if (s->pipeline) {
+    std::swap(s->Astate, s->Astate_alt);      // the frame's smoothed state
+    WH_CU(cudaEventRecord(s->ev_spec, ss));
+    WH_CU(cudaStreamWaitEvent(sp, s->ev_spec, 0));
+  }
+  if (wait_search) WH_CU(cudaStreamWaitEvent(sp, wait_search, 0));
+  s->st = sp;                                 // the search helpers enqueue on s->st
   int nlaunch = 3;
+  int rc = WH_OK;
   if (s->mlp) {
-    const int rc = learned_search(s);
-    if (rc != WH_OK) return rc;
+    rc = learned_search(s);
     nlaunch = 4;
   } else if (s->use_tc) {
     AutocorrTcArgs ta{};
     fill_tc_args(s, ta);
-    e = launch_autocorr_convert(ta, s->st);
-    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation convert kernel");
-    e = tc_autocorr_shortlist(s->d_a16, s->kg, s->d_table, s->kg, s->H * s->W, s->M * s->M, s->ntile,
-                              s->L * s->L, s->tc_bf16 != 0, s->tc_mode == 0 ? s->d_l1 : nullptr,
-                              s->d_cval, s->d_cidx, s->d_err, s->st);
-    if (e != cudaSuccess) return set_cuda_err(e, "tensor-core autocorrelation");
-    e = launch_autocorr_rerank(ta, s->st);
-    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation re-rank kernel");
+    e = launch_autocorr_convert(ta, sp);
+    if (e != cudaSuccess) rc = set_cuda_err(e, "autocorrelation convert kernel");
+    if (rc == WH_OK) {
+      e = tc_autocorr_shortlist(s->d_a16, s->kg, s->d_table, s->kg, s->H * s->W, s->M * s->M, s->ntile,
+                                s->L * s->L, s->tc_bf16 != 0, s->tc_mode == 0 ? s->d_l1 : nullptr,
+                                s->d_cval, s->d_cidx, s->d_err, sp);
+      if (e != cudaSuccess) rc = set_cuda_err(e, "tensor-core autocorrelation");
+    }
+    if (rc == WH_OK && (e = launch_autocorr_rerank(ta, sp)) != cudaSuccess)
+      rc = set_cuda_err(e, "autocorrelation re-rank kernel");
     nlaunch = 5;
   } else {
     AutocorrArgs aa{};
@@ -494,16 +561,23 @@ static int push_kernels(wh_stream* s, const float* src) {
     aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
     aa.vidx = s->vidx; aa.vx = s->vx; aa.vy = s->vy; aa.rs_out = nullptr;
     aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx; aa.pix_list = nullptr; aa.n_list = nullptr;
-    e = launch_autocorr(aa, s->st);
-    if (e != cudaSuccess) return set_cuda_err(e, "autocorrelation kernel");
+    if ((e = launch_autocorr(aa, sp)) != cudaSuccess) rc = set_cuda_err(e, "autocorrelation kernel");
   }
-  if (ev) WH_CU(cudaEventRecord(ev[2], s->st));
-  PefArgs pa{};
-  pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
-  pa.obs = s->obs[1 - s->cur]; pa.vidx = s->vidx; pa.hw = s->d_hw; pa.whitened = s->whitened;
-  e = launch_pef(pa, s->st);
-  if (e != cudaSuccess) return set_cuda_err(e, "PEF kernel");
-  if (ev) WH_CU(cudaEventRecord(ev[3], s->st));
+  if (rc == WH_OK && ev && (e = cudaEventRecord(ev[2], sp)) != cudaSuccess) rc = set_cuda_err(e, "cudaEventRecord");
+  if (rc == WH_OK) {
+    PefArgs pa{};
+    pa.H = s->H; pa.W = s->W; pa.M = s->M; pa.Mz = s->Mz; pa.L = s->L; pa.mpz = s->mpz;
+    pa.obs = s->obs[1 - s->cur]; pa.vidx = s->vidx; pa.hw = s->d_hw; pa.whitened = s->whitened;
+    if ((e = launch_pef(pa, sp)) != cudaSuccess) rc = set_cuda_err(e, "PEF kernel");
+  }
+  if (rc == WH_OK && ev && (e = cudaEventRecord(ev[3], sp)) != cudaSuccess) rc = set_cuda_err(e, "cudaEventRecord");
+  if (rc == WH_OK && s->pipeline) {
+    if ((e = cudaEventRecord(s->ev_pef[k], sp)) != cudaSuccess) rc = set_cuda_err(e, "cudaEventRecord");
+    s->pef_used[k] = 1;
+    s->pipe_work = 1;
+  }
+  s->st = user;
+  if (rc != WH_OK) return rc;
   g_launches.fetch_add(nlaunch);
   s->cur = 1 - s->cur;
   s->t += 1;
@@ -514,15 +588,24 @@ int wh_push_frame(wh_stream* s, const float* frame, int is_device) {
   if (!s || !frame) return WH_EINVAL;
   const size_t npix = size_t(s->H) * s->W;
   const float* src = frame;
+  const cudaStream_t ss = s->pipeline ? s->st_s : s->st;
+  const cudaStream_t sp = s->pipeline ? s->st_p : s->st;
   if (s->as) {   // the buffers in use may still be read by an asynchronous output copy
     for (int b = 0; b < 2; ++b)
-      if (s->as->used[b]) WH_CU(cudaStreamWaitEvent(s->st, s->as->ev_out[b], 0));
+      if (s->as->used[b]) {
+        WH_CU(cudaStreamWaitEvent(ss, s->as->ev_out[b], 0));
+        WH_CU(cudaStreamWaitEvent(sp, s->as->ev_out[b], 0));
+      }
   }
+  cudaEvent_t wait_spec = nullptr;
   if (!is_device) {
-    WH_CU(cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, s->st));
+    WH_CU(cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, ss));
     src = s->frame;
+  } else if (s->pipeline) {      // a device frame is ready in the caller's stream order
+    WH_CU(cudaEventRecord(s->ev_user, s->st));
+    wait_spec = s->ev_user;
   }
-  return push_kernels(s, src);
+  return push_kernels(s, src, wait_spec);
 }
 
 static int init_async(wh_stream* s) {
@@ -561,12 +644,10 @@ int wh_push_frame_async(wh_stream* s, const float* frame_host, float* whitened_h
   WH_CU(cudaMemcpyAsync(a->frame[b], frame_host, bytes, cudaMemcpyHostToDevice, a->in));
   WH_CU(cudaEventRecord(a->ev_in[b], a->in));
   // kernels: after the input copy, and after the set's previous outputs were copied out
-  WH_CU(cudaStreamWaitEvent(s->st, a->ev_in[b], 0));
-  if (a->used[b]) WH_CU(cudaStreamWaitEvent(s->st, a->ev_out[b], 0));
   s->frame = a->frame[b]; s->whitened = a->w[b]; s->vx = a->vx[b]; s->vy = a->vy[b];
-  rc = push_kernels(s, a->frame[b]);
+  rc = push_kernels(s, a->frame[b], a->ev_in[b], a->used[b] ? a->ev_out[b] : nullptr);
   if (rc != WH_OK) return rc;
-  WH_CU(cudaEventRecord(a->ev_comp[b], s->st));
+  WH_CU(cudaEventRecord(a->ev_comp[b], s->pipeline ? s->st_p : s->st));
   // output copies
   WH_CU(cudaStreamWaitEvent(a->out, a->ev_comp[b], 0));
   if (whitened_host) WH_CU(cudaMemcpyAsync(whitened_host, a->w[b], bytes, cudaMemcpyDeviceToHost, a->out));
@@ -587,8 +668,17 @@ int wh_stream_selftest_status(wh_stream* s, int code) {
   return WH_OK;
 }
 
+int wh_stream_join(wh_stream* s) {
+  if (!s) return WH_EINVAL;
+  return join_pipeline(s);
+}
+
 int wh_stream_sync(wh_stream* s) {
   if (!s) return WH_EINVAL;
+  if (s->pipeline) {
+    WH_CU(cudaStreamSynchronize(s->st_s));
+    WH_CU(cudaStreamSynchronize(s->st_p));
+  }
   WH_CU(cudaStreamSynchronize(s->st));
   if (s->as) {
     WH_CU(cudaStreamSynchronize(s->as->in));
@@ -648,6 +738,7 @@ static int copy_out(wh_stream* s, void* dst, const void* src, size_t bytes, int 
 
 int wh_read_whitened(wh_stream* s, float* out, int is_device, long long* frame_index) {
   if (!s || !out) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (s->t < s->mpz + 1) return WH_ENOTREADY;
   if (frame_index) *frame_index = s->t - 1 - s->mpz;
   return copy_out(s, out, s->whitened, sizeof(float) * size_t(s->H) * s->W, is_device);
@@ -656,6 +747,7 @@ int wh_read_whitened(wh_stream* s, float* out, int is_device, long long* frame_i
 int wh_read_velocity(wh_stream* s, float* vx, float* vy, int* vidx, int is_device,
                      long long* frame_index) {
   if (!s) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (s->t < 1) return WH_ENOTREADY;
   if (frame_index) *frame_index = s->t - 1;
   const size_t n = size_t(s->H) * s->W;
@@ -668,6 +760,7 @@ int wh_read_velocity(wh_stream* s, float* vx, float* vy, int* vidx, int is_devic
 
 int wh_read_spectrum(wh_stream* s, int kind, void* out, int is_device) {
   if (!s || !out) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (s->t < 1) return WH_ENOTREADY;
   const size_t nb = size_t(s->H) * s->W * s->M * s->M * s->Mz;
   if (kind == WH_SPEC_RAW) {
@@ -687,6 +780,7 @@ int wh_read_spectrum(wh_stream* s, int kind, void* out, int is_device) {
 
 int wh_read_autocorr(wh_stream* s, float* out, int is_device) {
   if (!s || !out) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (s->t < 1) return WH_ENOTREADY;
   const size_t n = size_t(s->H) * s->W * s->L * s->L;
   if (!s->d_rs) WH_CU(cudaMalloc((void**)&s->d_rs, sizeof(float) * n));
@@ -713,6 +807,7 @@ int wh_stream_info(const wh_stream* s, int* grid_len, int* delay_z, int* band,
 
 int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
   if (!s) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   int h = 0;
   WH_CU(cudaStreamSynchronize(s->st));
   if (s->d_nfb) WH_CU(cudaMemcpy(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost));
@@ -771,6 +866,7 @@ int wh_stream_set_features(wh_stream* s, int enable) {
 
 int wh_read_features(wh_stream* s, void* out, int is_device, int* ld) {
   if (!s || !s->d_feat) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (ld) *ld = s->feat_ld;
   if (!out) return WH_OK;
   return copy_out(s, out, s->d_feat, 2 * size_t(s->H) * s->W * s->feat_ld, is_device);
@@ -801,6 +897,7 @@ int wh_stream_set_learned(wh_stream* s, wh_mlp* mlp, float conf_threshold) {
 
 int wh_stream_learned_stats(wh_stream* s, long long* frames, long long* fallback_pixels) {
   if (!s) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   long long h = 0;
   if (s->d_nfb_total) {
     WH_CU(cudaMemcpyAsync(&h, s->d_nfb_total, sizeof(long long), cudaMemcpyDeviceToHost, s->st));
@@ -813,6 +910,7 @@ int wh_stream_learned_stats(wh_stream* s, long long* frames, long long* fallback
 
 int wh_output_pointers(wh_stream* s, float** whitened, float** vx, float** vy, int** vidx) {
   if (!s) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (whitened) *whitened = s->whitened;
   if (vx) *vx = s->vx;
   if (vy) *vy = s->vy;

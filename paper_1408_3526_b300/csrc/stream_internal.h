@@ -66,6 +66,14 @@ struct wh_stream {
     int par;                   // set of the next push
   };
   Async* as;
+  // frame pipeline (wh_params.pipeline): spectrum kernels on st_s, search and
+  // PEF on st_p; the smoothed state alternates between Astate and Astate_alt
+  int pipeline;
+  cudaStream_t st_s, st_p;
+  cudaEvent_t ev_user, ev_spec, ev_join, ev_pef[2];
+  int pef_used[2];
+  int pipe_work;              // kernels were enqueued since the last join
+  float* Astate_alt;
   // threshold detector scratch (wh_detect)
   void* d_det;
   size_t det_bytes;
@@ -80,4 +88,6 @@ struct wh_stream {
 // error text of the calling thread (512 bytes), CUDA failure -> WH_ECUDA, launch counter
 char* wh_error_buffer();
 int wh_cuda_fail(cudaError_t e, const char* what);
+// order the stream's own CUDA stream after its frame-pipeline work (no-op without the pipeline)
+int wh_join_pipeline(wh_stream* s);
 void wh_count_launches(long long n);

@@ -37,13 +37,15 @@ class WhitenStream:
 
     Parameters follow ``wh_create_stream``: frame size, spatial window M
     (odd), temporal order Mz, velocity grid (vmax, step), and the optional
-    band B, output delay m'_z, smoother pole alpha, precision mode.
+    band B, output delay m'_z, smoother pole alpha, precision mode, and
+    ``pipeline`` (overlap consecutive frames on two internal CUDA streams;
+    identical results).
     """
 
     def __init__(self, h: int, w: int, window: int, temporal_order: int, vmax: float,
                  step: float, band: int | None = None, delay_z: int | None = None,
                  alpha: float | None = None, precision: int = 0, debug_dump: bool = False,
-                 cuda_stream=None):
+                 cuda_stream=None, pipeline: bool = False):
         self.lib = _abi.load()
         self.h, self.w, self.M, self.Mz = int(h), int(w), int(window), int(temporal_order)
         p = _abi.wh_params()
@@ -56,6 +58,7 @@ class WhitenStream:
             p.alpha = float(alpha)
         p.precision = int(precision)
         p.debug_dump = int(bool(debug_dump))
+        p.pipeline = int(bool(pipeline))
         if cuda_stream is None:
             torch = _torch()
             cuda_stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
@@ -144,6 +147,10 @@ class WhitenStream:
 
     def sync(self) -> None:
         check(self.lib.wh_stream_sync(self._s), "wh_stream_sync")
+
+    def join(self) -> None:
+        """Order the stream's CUDA stream after all enqueued work (no host wait)."""
+        check(self.lib.wh_stream_join(self._s), "wh_stream_join")
 
     def _alloc(self, shape, dtype, device):
         if device:

@@ -1,0 +1,86 @@
+"""Frame pipeline (wh_params.pipeline): the spectrum kernel of frame t+1 overlaps
+the search and PEF of frame t on two internal CUDA streams, with the smoothed
+state double-buffered.  Results must be bit-identical to the serial stream,
+for device and host frames, the synchronous and the pipelined host push, and
+both search engines (needs a B300)."""
+import numpy as np
+import pytest
+
+from paper_1408_3526_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+H, W, M, MZ, VMAX, VSTEP, T = 96, 120, 9, 4, 2.0, 0.25, 16
+DELAY = (MZ - 1) // 2
+
+
+def _run(frames, pipeline, precision=0, device=True, debug=False):
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    out = []
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, precision=precision, pipeline=pipeline,
+                      debug_dump=debug) as s:
+        dev = torch.from_numpy(frames).cuda()
+        for t in range(frames.shape[0]):
+            s.push(dev[t] if device else np.ascontiguousarray(frames[t]))
+            vx, vy, vi, _ = s.read_velocity()
+            w = s.read_whitened()[0] if t >= DELAY else None
+            out.append((vx, vy, vi, w))
+        if debug:
+            from paper_1408_3526_b300 import _abi
+            out.append(s.read_spectrum(_abi.WH_SPEC_WINDOWED))
+            out.append(s.read_autocorr())
+    return out
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        if isinstance(x, tuple):
+            for u, v in zip(x, y):
+                if u is None:
+                    assert v is None
+                else:
+                    assert np.array_equal(u, v)
+        else:
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [0, 16], ids=["cuda_cores", "tc_shortlist_rerank"])
+def test_pipeline_identical_to_serial(precision):
+    fr = scenes.config1_scene(T=T, H=H, W=W, seed=9).frames.astype(np.float32)
+    _same(_run(fr, False, precision), _run(fr, True, precision))
+
+
+def test_pipeline_host_frames_and_debug_reads():
+    fr = scenes.config1_scene(T=10, H=H, W=W, seed=10).frames.astype(np.float32)
+    _same(_run(fr, False, device=False, debug=True), _run(fr, True, device=False, debug=True))
+
+
+def test_pipeline_unread_frames_then_async_push():
+    """Frames pushed back to back without reads (the overlapped case), then the
+    pipelined host push with double-buffered outputs."""
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    fr = scenes.config1_scene(T=T, H=H, W=W, seed=11).frames.astype(np.float32)
+    ref = []
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP) as s:
+        for t in range(T):
+            s.push(np.ascontiguousarray(fr[t]))
+            ref.append((s.read_velocity()[0].copy(), s.read_whitened()[0].copy() if t >= DELAY else None))
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, pipeline=True) as s:
+        dev = torch.from_numpy(fr).cuda()
+        for t in range(T // 2):
+            s.push(dev[t])
+        vx = s.read_velocity()[0]
+        assert np.array_equal(vx, ref[T // 2 - 1][0])
+        pin = [torch.from_numpy(fr[t].copy()).pin_memory() for t in range(T)]
+        outs = [[torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+                for _ in range(T)]
+        for t in range(T // 2, T):
+            s.push_async(pin[t], outs[t][0], outs[t][1], None)
+        s.sync()
+        for t in range(T // 2, T):
+            assert np.array_equal(outs[t][1].numpy(), ref[t][0]), t
+            assert np.array_equal(outs[t][0].numpy(), ref[t][1]), t
