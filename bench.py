@@ -186,14 +186,14 @@ def cpu_baseline(frames, seconds_target=12.0):
     T = 8
     crop = (232, 296, h, w)
     o.run(frames[:T], crop=crop, nthreads=cores)          # untimed: thread pool and caches
+    reps = 0
     t0 = time.perf_counter()
-    o.run(frames[:T], crop=crop, nthreads=cores)
-    dt1 = time.perf_counter() - t0
-    reps = max(1, int(round(seconds_target / max(dt1, 1e-3))))
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    while True:                                            # whole repetitions, ~seconds_target in all
         o.run(frames[:T], crop=crop, nthreads=cores)
-    dt = time.perf_counter() - t0
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target or reps >= 1000:
+            break
     px = h * w * T * reps
     return {"value": round(px / dt / 1e6, 6), "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
             "sample": f"{h}x{w} crop x {T} frames x {reps} reps of the 512x640 workload "

@@ -38,7 +38,9 @@
 // Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1), box sums(i+1)}.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
@@ -658,10 +660,13 @@ cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
 
 // Upload the constant tables (all window sizes and temporal orders, per device).
 cudaError_t spectrum_init_constants() {
-  static bool done[64] = {false};
+  static std::atomic<bool> done[64];
+  static std::mutex mu;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && done[dev]) return cudaSuccess;
+  if (dev < 64 && done[dev].load()) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);      // one upload per device even with concurrent creators
+  if (dev < 64 && done[dev].load()) return cudaSuccess;
   const double pi = 3.14159265358979323846;
   float2 w[7][kMaxM], c[7][kMaxM];
   for (int mi = 0; mi < 7; ++mi) {
@@ -709,7 +714,7 @@ cudaError_t spectrum_init_constants() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hz, hz, sizeof(hz));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cz, cz, sizeof(cz));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sz, sz, sizeof(sz));
-  if (e == cudaSuccess && dev < 64) done[dev] = true;
+  if (e == cudaSuccess && dev < 64) done[dev].store(true);
   return e;
 }
 

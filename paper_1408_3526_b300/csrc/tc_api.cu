@@ -24,8 +24,11 @@ __global__ void wait_selftest_kernel(uint64_t limit_ns, int* flag) {
 }
 
 thread_local char g_err2[256] = "";
+// One error flag per (host thread, device): concurrent calls from different
+// threads never share a flag.  (Allocated once per thread and device; freed at
+// process exit with the context.)
 int* device_err_flag() {
-  static int* flags[64] = {nullptr};
+  thread_local int* flags[64] = {nullptr};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return nullptr;
