@@ -155,7 +155,12 @@ struct SG {
   static constexpr size_t O_SROW = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [3][SROW]
   static constexpr size_t O_MBAR = al16(O_SROW + 4ull * 3 * SROW);             // uint64 [3]
   static constexpr size_t O_OFFS = al16(O_MBAR + 8ull * 3);                    // float2 [NPL]
-  static constexpr size_t SMEM = al16(O_OFFS + 8ull * NPL);
+  // learned-estimator features (used only when they are requested)
+  static constexpr int NBINS = M * M * MZ;
+  static constexpr size_t O_FGS = al16(O_OFFS + 8ull * NPL);                   // int   [NBINS] gather
+  static constexpr size_t O_FPART = al16(O_FGS + 4ull * NBINS);                // float [TW][NH1]
+  static constexpr size_t O_FTOT = al16(O_FPART + 4ull * TW * NH1);            // float [TW]
+  static constexpr size_t SMEM = al16(O_FTOT + 4ull * TW);
   static_assert(RW <= 32, "the observer warp covers the row segment");
   static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
   static_assert(NBT * RB + NOB * RD >= NDT, "every reduction task has a thread");
@@ -263,6 +268,12 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   float* srow = reinterpret_cast<float*>(smem_raw + G::O_SROW);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + G::O_MBAR);
   float2* offs = reinterpret_cast<float2*>(smem_raw + G::O_OFFS);
+  int* fgs = reinterpret_cast<int*>(smem_raw + G::O_FGS);
+  float* fpart = reinterpret_cast<float*>(smem_raw + G::O_FPART);
+  float* ftot = reinterpret_cast<float*>(smem_raw + G::O_FTOT);
+  const bool feat = a.feat != nullptr;
+  if (feat)
+    for (int i = tid; i < G::NBINS; i += NTHR) fgs[i] = a.feat_gather[i];
 
   // Power scale (Mz/sqrt(N))^2 and the 1/16 of the 4x Hann taps, as sig^2 on
   // the x-DFT weights and box sums (everything before the power is linear).
@@ -522,14 +533,23 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
         // P(h, kz) for the slots kz = 0, +j, -j (= P(-h, +j)), Mz/2 of this h:
         // offsets x*PS + (c*M + ky + K) with c the channel of (plane, +-hx)
         const int op = x * PS + hi + K, om = x * PS - hi + K;
-        float Ac = pbuf[op], As = 0.f;
+        const float p0 = pbuf[op];
+        float Ac = p0, As = 0.f, ps = p0;
 #pragma unroll
         for (int j = 1; j <= J; ++j) {
           const float pp = pbuf[op + (G::base(j) + K) * M], pm = pbuf[om + (G::base(j) + K) * M];
           Ac = fmaf(pp + pm, c_cz[ZI][j], Ac);
           As = fmaf(pp - pm, c_sz[ZI][j], As);
+          ps += pp + pm;
         }
-        if (EVEN) Ac -= pbuf[op + G::base(NPL - 1) * M];
+        if (EVEN) {
+          const float pn = pbuf[op + G::base(NPL - 1) * M];
+          Ac -= pn;
+          ps += pn;
+        }
+        // features: this h's share of the pixel's power sum over all M^2 Mz bins
+        // (the bins at -h repeat the same values, except for h = 0)
+        if (feat) fpart[x * NH1 + hi] = hi > 0 ? 2.f * ps : ps;
         float* sp = st + x * KPAD + hi;
         sp[0] = fmaf(oma, Ac, alpha * sp[0]);
         if (hi > 0) sp[NH] = fmaf(oma, As, alpha * sp[NH]);
@@ -542,23 +562,38 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
         for (int q = 0; q < RD; ++q) one(dbase + q * dstride);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the bulk store
-      // learned-estimator features of this output row: one warp per pixel
-      if (a.feat != nullptr) {
+      // learned-estimator features of this output row, (log2(P / sum P + 1e-6) + 10) / 10
+      // of every bin in [kz][ky][kx] order, BF16, written 8 bins per 16-byte store
+      if (feat) {
         constexpr int NDW = NTW / 32;
-        const int wid = tid >> 5;
-        constexpr int nbins = M * M * MZ;
-        for (int x = wid; x < TW; x += NDW) {
-          if (x0 + x >= W) continue;
-          const float* pb = pbuf + x * PS;
-          float tot = 0.f;
-          for (int b = lane; b < nbins; b += 32) tot += pb[a.feat_gather[b]];
+        asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");   // all partial sums of the row
+        for (int x = tid >> 5; x < TW; x += NDW) {
+          float t = 0.f;
+          for (int h = lane; h < NH1; h += 32) t += fpart[x * NH1 + h];
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+          for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+          if (lane == 0) ftot[x] = t;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");
+        const int nv = a.feat_ld / 8;
+        for (int task = tid; task < TW * nv; task += NTW) {
+          const int x = task / nv, v = task - x * nv;
+          if (x0 + x >= W) continue;
+          const float tot = ftot[x];
           const float inv = tot > 0.f ? 1.f / tot : 0.f;
-          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.feat) + (size_t(yo) * W + x0 + x) * a.feat_ld;
-          for (int b = lane; b < a.feat_ld; b += 32)
-            dst[b] = __float2bfloat16(
-                b < nbins ? 0.1f * (__log2f(fmaf(pb[a.feat_gather[b]], inv, 1e-6f)) + 10.f) : 0.f);
+          const float* pb = pbuf + x * PS;
+          uint32_t packed[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int b0 = 8 * v + 2 * q;
+            const float f0 = b0 < G::NBINS ? 0.1f * (__log2f(fmaf(pb[fgs[b0]], inv, 1e-6f)) + 10.f) : 0.f;
+            const float f1 = b0 + 1 < G::NBINS ? 0.1f * (__log2f(fmaf(pb[fgs[b0 + 1]], inv, 1e-6f)) + 10.f) : 0.f;
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(f0, f1);
+            packed[q] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.feat) +
+                                                (size_t(yo) * W + x0 + x) * a.feat_ld) + v;
+          *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
       }
     };
