@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* accum = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* bias_s = reinterpret_cast<float*>(tmem_slot + 4);      // [BN] bias of this N tile
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
@@ -74,6 +75,9 @@ __global__ void __launch_bounds__(192, 1)
     tc::tmem_alloc(tmem_slot, BN);
     tc::tmem_relinquish();
   }
+  if (warp >= 2)
+    for (int i = threadIdx.x - 64; i < BN; i += 128)
+      bias_s[i] = (g.bias && n0 + i < g.N) ? g.bias[n0 + i] : 0.f;
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -153,13 +157,43 @@ __global__ void __launch_bounds__(192, 1)
             else { tv[3] = v; ti[3] = col; }
           }
         }
+      } else if (g.vec && col0 + 32 <= g.N) {
+        // a full 32-column chunk of this thread's row: 16-byte vector stores
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias_s[c * 32 + j];
+        if (g.preact) {
+          float4* pp = reinterpret_cast<float4*>(g.preact + size_t(row) * g.ldp + col0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) pp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (g.act) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = gelu_tanh(v[j]);
+        }
+        if (g.epi == EPI_F32) {
+          float4* cp = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + size_t(row) * g.ldc + col0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+          uint4* cp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.C) + size_t(row) * g.ldc + col0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+              w[e] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            cp[q] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = col0 + j;
           if (col >= g.N) break;
-          float v = __uint_as_float(r[j]);
-          if (g.bias) v += g.bias[col];
+          float v = __uint_as_float(r[j]) + bias_s[c * 32 + j];
           if (g.preact) g.preact[size_t(row) * g.ldp + col] = v;
           if (g.act) v = gelu_tanh(v);
           if (g.epi == EPI_F32) reinterpret_cast<float*>(g.C)[size_t(row) * g.ldc + col] = v;
@@ -220,7 +254,7 @@ cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, 
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, g.M, g.K, lda, kBM, g.bf16) || !make_map(&mb, B, g.N, g.K, ldb, BN, g.bf16))
     return cudaErrorInvalidValue;
-  const size_t smem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 1) * 8 + 16;
+  const size_t smem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 1) * 8 + 16 + 4 * BN;
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN);
@@ -234,9 +268,14 @@ bool make_map_2b(CUtensorMap* m, const void* ptr, int rows, int K, int ld, int b
   return make_map(m, ptr, rows, K, ld, box_rows, bf16);
 }
 
-cudaError_t tc_gemm(const GemmArgs& g, const void* A, int lda, const void* B, int ldb, int bn,
+cudaError_t tc_gemm(const GemmArgs& g_in, const void* A, int lda, const void* B, int ldb, int bn,
                     cudaStream_t st) {
-  if (g.M < 1 || g.N < 1 || g.K < 1 || !g.err) return cudaErrorInvalidValue;
+  if (g_in.M < 1 || g_in.N < 1 || g_in.K < 1 || !g_in.err) return cudaErrorInvalidValue;
+  GemmArgs g = g_in;
+  const auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  g.vec = g.epi != EPI_TOPK && g.C && a16(g.C) &&
+          (g.epi == EPI_F32 ? (g.ldc % 4 == 0) : (g.ldc % 8 == 0)) &&
+          (!g.preact || (a16(g.preact) && g.ldp % 4 == 0));
   switch (bn) {
     case 64: return launch_bn<64>(g, A, lda, B, ldb, st);
     case 128: return launch_bn<128>(g, A, lda, B, ldb, st);

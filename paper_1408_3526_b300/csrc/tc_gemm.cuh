@@ -20,6 +20,7 @@ struct GemmArgs {
   int* cand_idx;
   int n_valid;          // EPI_TOPK: columns >= n_valid are ignored
   int* err;             // device error flag (0 = ok)
+  int vec;              // set by tc_gemm: C (and preact) rows allow 16-byte vector stores
 };
 
 // A: [M][lda] K-major, B: [N][ldb] K-major (2-byte elements, 16-byte aligned rows).
