@@ -215,6 +215,196 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// Persistent variant for many output tiles (EPI_F32 / EPI_BF16): one CTA per
+// SM walks the 128 x BN tiles t = blockIdx.x, +gridDim.x, ... (N tiles
+// fastest).  A and B K-blocks stream through one 4-stage ring whose counters
+// run on across tiles; the accumulator is double-buffered in TMEM (2 x BN
+// columns), so the epilogue of one tile overlaps the loads and MMAs of the
+// next.  Same warp roles, bounded waits and error flag as tc_gemm_kernel.
+template <int BN>
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, const uint32_t (&r)[32], int row, int col0,
+                                               const float* bias) {
+  if (row >= g.M) return;
+  if (g.vec && col0 + 32 <= g.N) {
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + (bias ? __ldg(bias + col0 + j) : 0.f);
+    if (g.preact) {
+      float4* pp = reinterpret_cast<float4*>(g.preact + size_t(row) * g.ldp + col0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    if (g.act) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = gelu_tanh(v[j]);
+    }
+    if (g.epi == EPI_F32) {
+      float4* cp = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + size_t(row) * g.ldc + col0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+      uint4* cp = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.C) + size_t(row) * g.ldc + col0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+          w[e] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+        cp[q] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int col = col0 + j;
+      if (col >= g.N) break;
+      float v = __uint_as_float(r[j]) + (bias ? __ldg(bias + col) : 0.f);
+      if (g.preact) g.preact[size_t(row) * g.ldp + col] = v;
+      if (g.act) v = gelu_tanh(v);
+      if (g.epi == EPI_F32) reinterpret_cast<float*>(g.C)[size_t(row) * g.ldc + col] = v;
+      else reinterpret_cast<__nv_bfloat16*>(g.C)[size_t(row) * g.ldc + col] = __float2bfloat16(v);
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    tc_pgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base_u32 = tc::smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+  uint8_t* sA = smem;                                    // kStages x 16 KB
+  uint8_t* sB = smem + kStages * kBM * kBK * 2;          // kStages x BN*128 B
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * BN * kBK * 2);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;                  // [2]
+  uint64_t* acc_empty = acc_full + 2;                    // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (g.K + kBK - 1) / kBK;
+  const int nN = (g.N + BN - 1) / BN, nM = (g.M + kBM - 1) / kBM;
+  const int ntiles = nM * nN, G = gridDim.x;
+  constexpr uint32_t kStageBytes = (kBM + BN) * kBK * 2;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < kStages; ++s) {
+        tc::mbar_init(&full[s], 1);
+        tc::mbar_init(&empty[s], 1);
+      }
+      for (int b = 0; b < 2; ++b) {
+        tc::mbar_init(&acc_full[b], 1);
+        tc::mbar_init(&acc_empty[b], 4);
+      }
+      *abort_flag = 0;
+      tc::fence_mbar_init();
+      tc::tma_prefetch_desc(&tmA);
+      tc::tma_prefetch_desc(&tmB);
+    }
+    __syncwarp();
+    tc::tmem_alloc(tmem_slot, 2 * BN);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&](int code) {
+    atomicExch(g.err, code);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int sc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += G) {
+      const int m = t / nN, n = t - m * nN;
+      for (int kb = 0; kb < nk; ++kb, ++sc) {
+        const int s = sc % kStages;
+        if (sc >= kStages && !tc::mbar_wait(&empty[s], ((sc / kStages) - 1) & 1, kWaitNs)) {
+          fail(21);
+          ok = false;
+          break;
+        }
+        if (*abort_flag) { ok = false; break; }
+        tc::mbar_expect_tx(&full[s], kStageBytes);
+        tc::tma_load_2d(sA + s * kBM * kBK * 2, &tmA, &full[s], kb * kBK, m * kBM);
+        tc::tma_load_2d(sB + s * BN * kBK * 2, &tmB, &full[s], kb * kBK, n * BN);
+      }
+    }
+    if (*abort_flag)   // let the copies still in flight land before the CTA exits (bounded)
+      for (int i = sc > kStages ? sc - kStages : 0; i < sc; ++i)
+        tc::mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitNs);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = tc::idesc_f16(kBM, BN, g.bf16 != 0);
+    int sc = 0, tcount = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += G, ++tcount) {
+      const int acc = tcount & 1;
+      if (tcount >= 2 && !tc::mbar_wait(&acc_empty[acc], ((tcount >> 1) - 1) & 1, kWaitNs)) {
+        fail(22);
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t d = tmem + uint32_t(acc * BN);
+      for (int kb = 0; kb < nk; ++kb, ++sc) {
+        const int s = sc % kStages;
+        if (!tc::mbar_wait(&full[s], (sc / kStages) & 1, kWaitNs)) { fail(23); ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(sA + s * kBM * kBK * 2);
+        const uint32_t b0 = tc::smem_u32(sB + s * BN * kBK * 2);
+#pragma unroll
+        for (int k = 0; k < kBK / 16; ++k)
+          tc::mma_f16(d, tc::sdesc_sw128(a0 + 32 * k), tc::sdesc_sw128(b0 + 32 * k), idesc,
+                      (kb > 0 || k > 0) ? 1u : 0u);
+        tc::mma_commit(&empty[s]);
+      }
+      if (ok) tc::mma_commit(&acc_full[acc]);
+    }
+    if (!ok) {                       // release the epilogue so it can see the flag and stop
+      tc::mbar_arrive(&acc_full[0]);
+      tc::mbar_arrive(&acc_full[1]);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;                   // TMEM lane quadrant of this warp
+    int tcount = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++tcount) {
+      const int acc = tcount & 1;
+      const bool w = tc::mbar_wait(&acc_full[acc], (tcount >> 1) & 1, 4 * kWaitNs);
+      if (!w) fail(24);
+      tc::tc_fence_after();
+      if (!w || *abort_flag) break;
+      const int m = t / nN, n = t - m * nN;
+      const int row = m * kBM + q * 32 + lane;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * BN + c * 32), r);
+        tc::tmem_ld_wait();
+        epilogue_chunk<BN>(g, r, row, n * BN + c * 32, g.bias);
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
 // ---- host side: tensor maps through the driver entry point -----------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -254,6 +444,20 @@ cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, 
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, g.M, g.K, lda, kBM, g.bf16) || !make_map(&mb, B, g.N, g.K, ldb, BN, g.bf16))
     return cudaErrorInvalidValue;
+  const long long ntiles = (long long)((g.M + kBM - 1) / kBM) * ((g.N + BN - 1) / BN);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (g.epi != EPI_TOPK && ntiles >= 4LL * nsm) {
+    // many tiles: one persistent CTA per SM with a double-buffered accumulator
+    const size_t psmem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 4) * 8 + 16;
+    ResidentShape rs{};
+    cudaError_t e = resident_shape(tc_pgemm_kernel<BN>, 192, psmem, &rs);
+    if (e != cudaSuccess) return e;
+    const long long grid = ntiles < (long long)nsm ? ntiles : (long long)nsm;
+    tc_pgemm_kernel<BN><<<unsigned(grid), 192, psmem, st>>>(ma, mb, g);
+    return cudaGetLastError();
+  }
   const size_t smem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 1) * 8 + 16 + 4 * BN;
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
