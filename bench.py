@@ -133,7 +133,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -143,6 +143,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout_s=3.0):
+        """Block until the sampler has printed its first line (or timeout)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout_s:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -208,7 +214,19 @@ def run_reference(args):
     frames = make_frames()
     o = oracle.Oracle(M, MZ, VMAX, VSTEP)
     cores = os.cpu_count() or 1
-    h, w, T = 24, 32, 6
+    T = 6
+    # per-step sample: the largest crop whose K + W steps fit in about 90 s
+    # (the oracle's cost grows with the crop plus its (M - 1)-pixel halo)
+    crops = [(24, 32), (16, 24), (12, 16), (8, 12), (8, 8)]
+    t0 = time.perf_counter()
+    o.run(frames[:T], crop=(240, 300) + crops[0], nthreads=cores)
+    t_big = time.perf_counter() - t0
+    area = lambda c: (c[0] + M - 1) * (c[1] + M - 1)
+    h, w = crops[-1]
+    for c in crops:
+        if t_big * area(c) / area(crops[0]) * (args.steps + args.warmup) <= 90.0:
+            h, w = c
+            break
     crop = (240, 300, h, w)
 
     def step():
@@ -238,7 +256,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -280,7 +298,7 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
+    clocks.wait_first()
     n0 = kernel_launch_count()
     barrier()
     torch.cuda.synchronize()

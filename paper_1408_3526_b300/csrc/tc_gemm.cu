@@ -448,8 +448,10 @@ cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, 
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (g.epi != EPI_TOPK && ntiles >= 4LL * nsm) {
+  if (g.epi != EPI_TOPK && BN <= 128 && ntiles >= 4LL * nsm) {
     // many tiles: one persistent CTA per SM with a double-buffered accumulator
+    // (at BN = 256 the per-tile kernel measured faster: the loads, not the
+    // epilogue, bound that shape)
     const size_t psmem = 1024 + size_t(kStages) * (kBM + BN) * kBK * 2 + (2 * kStages + 4) * 8 + 16;
     ResidentShape rs{};
     cudaError_t e = resident_shape(tc_pgemm_kernel<BN>, 192, psmem, &rs);

@@ -173,17 +173,19 @@ def detection_snr_db(E, scene, t_frame, radius=1.0, exclude_sigmas=5.0):
     return 20.0 * math.log10(np.mean(peaks) / max(sd, 1e-30))
 
 
-def compare_on_sequence(net: MLP, sc, M=15, Mz=6, vmax=3.0, step=0.25, conf=0.8, warmup=12, snr_every=10):
+def compare_on_sequence(net: MLP, sc, M=15, Mz=6, vmax=3.0, step=0.25, conf=0.8, warmup=12, snr_every=10,
+                        modes=("plain", "learned")):
     """Run the plain and the learned mode on the same frames; returns timing
     (device ms per frame), velocity agreement with the plain search, share of
-    pixels decided by the network, and the detection SNR of both."""
+    pixels decided by the network, and the detection SNR of both.  ``modes``
+    may restrict the run to one of them (no agreement figures then)."""
     torch = _torch()
     from .stream import WhitenStream
     T, H, W = sc.frames.shape
     L = int(round(2 * vmax / step)) + 1
     out = {}
     vel = {}
-    for mode in ("plain", "learned"):
+    for mode in modes:
         st = torch.cuda.Stream()
         snr = []
         with WhitenStream(H, W, M, Mz, vmax, step, cuda_stream=st) as s:
@@ -205,7 +207,7 @@ def compare_on_sequence(net: MLP, sc, M=15, Mz=6, vmax=3.0, step=0.25, conf=0.8,
                     _, _, vi, _ = s.read_velocity(device=True)
                     if mode == "plain":
                         vel[t] = vi.clone()
-                    else:
+                    elif t in vel:
                         p = vel[t]
                         d = torch.maximum((vi % L - p % L).abs(), (vi // L - p // L).abs())
                         agree.append((float((d == 0).float().mean()), float((d <= 1).float().mean())))
@@ -218,12 +220,14 @@ def compare_on_sequence(net: MLP, sc, M=15, Mz=6, vmax=3.0, step=0.25, conf=0.8,
         rec = {"ms_per_frame": ms / n, "mpix_per_s": H * W / (ms / n) / 1e3,
                "snr_db_mean": float(np.nanmean(snr)), "snr_frames": len(snr)}
         if mode == "learned":
-            rec["velocity_identical_vs_plain"] = float(np.mean([a[0] for a in agree]))
-            rec["velocity_within_one_step_vs_plain"] = float(np.mean([a[1] for a in agree]))
+            if agree:
+                rec["velocity_identical_vs_plain"] = float(np.mean([a[0] for a in agree]))
+                rec["velocity_within_one_step_vs_plain"] = float(np.mean([a[1] for a in agree]))
             rec["share_decided_by_network"] = 1.0 - fb.value / max(fr.value, 1) / (H * W)
         out[mode] = rec
-    out["speedup_learned_over_plain"] = out["plain"]["ms_per_frame"] / out["learned"]["ms_per_frame"]
-    out["snr_difference_db"] = out["learned"]["snr_db_mean"] - out["plain"]["snr_db_mean"]
+    if "plain" in out and "learned" in out:
+        out["speedup_learned_over_plain"] = out["plain"]["ms_per_frame"] / out["learned"]["ms_per_frame"]
+        out["snr_difference_db"] = out["learned"]["snr_db_mean"] - out["plain"]["snr_db_mean"]
     return out
 
 
@@ -239,25 +243,34 @@ def main(argv=None):
     ap.add_argument("--eval-h", type=int, default=1024)
     ap.add_argument("--eval-w", type=int, default=1280)
     ap.add_argument("--conf", type=float, default=0.8)
-    ap.add_argument("--ckpt", default=None)
+    ap.add_argument("--ckpt", default=None, help="save the trained weights here")
+    ap.add_argument("--load", default=None, help="skip training and load these weights")
+    ap.add_argument("--modes", default="plain,learned", help="comma list of plain, learned")
+    ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    t0 = time.time()
-    X, V = generate_training_data(n_scenes=a.train_scenes, frames=a.train_frames, samples=a.samples)
-    t_data = time.time() - t0
     net = MLP(1350, 256, 128, 3, seed=1)
-    t0 = time.time()
-    hist = train(net, X, V, epochs=a.epochs, lr=1e-3, log=print)
-    _torch().cuda.synchronize()
-    t_train = time.time() - t0
+    if a.load:
+        net.load(a.load)
+        training = {"loaded": a.load}
+    else:
+        t0 = time.time()
+        X, V = generate_training_data(n_scenes=a.train_scenes, frames=a.train_frames, samples=a.samples)
+        t_data = time.time() - t0
+        t0 = time.time()
+        hist = train(net, X, V, epochs=a.epochs, lr=1e-3, log=print)
+        _torch().cuda.synchronize()
+        t_train = time.time() - t0
+        del X, V
+        training = {"samples": a.samples, "scenes": a.train_scenes, "epochs": a.epochs,
+                    "final_loss": hist[-1][0], "final_within_step": hist[-1][3],
+                    "data_seconds": t_data, "train_seconds": t_train}
     if a.ckpt:
         net.save(a.ckpt)
-    del X, V
     sc = scenes.config1_scene(T=a.eval_frames, H=a.eval_h, W=a.eval_w, seed=4)
-    rep = compare_on_sequence(net, sc, conf=a.conf)
-    rep["training"] = {"samples": a.samples, "scenes": a.train_scenes, "epochs": a.epochs,
-                       "final_loss": hist[-1][0], "final_within_step": hist[-1][3],
-                       "data_seconds": t_data, "train_seconds": t_train}
+    rep = compare_on_sequence(net, sc, conf=a.conf, warmup=min(a.warmup, a.eval_frames - 1),
+                              modes=tuple(m for m in a.modes.split(",") if m))
+    rep["training"] = training
     rep["eval"] = {"frames": a.eval_frames, "size": [a.eval_h, a.eval_w], "window": 15, "order": 6,
                    "grid": "+-3 step 0.25", "confidence_threshold": a.conf}
     print(json.dumps(rep))
