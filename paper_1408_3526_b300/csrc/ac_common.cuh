@@ -27,24 +27,24 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Copy the KP-float state row at src into dst with the 16 lanes j = 0..15 of
-// a half-warp (16-byte copies), and commit one group.
-template <int M>
+// Copy the KP-float state row at src into dst with the lanes j = 0..G-1 of a
+// lane group (16-byte copies), and commit one group.
+template <int M, int G = 16>
 __device__ __forceinline__ void prefetch_row(float* dst, const float* src, int j, bool valid) {
   if (valid)
-    for (int c = j; c < Geo<M>::KP / 4; c += 16) cp_async16(dst + 4 * c, src + 4 * c);
+    for (int c = j; c < Geo<M>::KP / 4; c += G) cp_async16(dst + 4 * c, src + 4 * c);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Q-sum elements e = j + 16 r handled by lane j: offsets hp, hm of A(kx, +ky)
-// and A(kx, -ky) and a sign bit conjugating the second for kx = 0 (A(0, -ky)
-// = conj A(0, ky) is stored as A(0, ky)); -1 past the end.
-template <int M, int QIT>
+// Q-sum elements e = j + G r handled by lane j of a G-lane group: offsets hp,
+// hm of A(kx, +ky) and A(kx, -ky) and a sign bit conjugating the second for
+// kx = 0 (A(0, -ky) = conj A(0, ky) is stored as A(0, ky)); -1 past the end.
+template <int M, int QIT, int G = 16>
 __device__ __forceinline__ void qsum_offsets(int j, int (&qoff)[QIT]) {
   constexpr int K = Geo<M>::K, NE = Geo<M>::NE;
 #pragma unroll
   for (int r = 0; r < QIT; ++r) {
-    const int e = j + 16 * r;
+    const int e = j + G * r;
     const int kx = e / K, ky = e % K + 1;
     int hp, hm, neg;
     if (kx == 0) { hp = ky; hm = ky; neg = 1; }
@@ -53,10 +53,12 @@ __device__ __forceinline__ void qsum_offsets(int j, int (&qoff)[QIT]) {
   }
 }
 
-// Q sums of the state row A (shared) into qbuf (shared), by the lanes of a half-warp.
-template <int M, int QIT>
+// Q sums of the state row A (shared) into qbuf (shared), by the G lanes of a
+// lane group (G >= K + 1).
+template <int M, int QIT, int G = 16>
 __device__ __forceinline__ void build_qsums(const float* A, float* qbuf, const int (&qoff)[QIT], int j) {
   constexpr int K = Geo<M>::K, NH = Geo<M>::NH;
+  static_assert(G >= K + 1, "one lane per Q(kx, 0)");
 #pragma unroll
   for (int r = 0; r < QIT; ++r) {
     const int t = qoff[r];
@@ -64,7 +66,7 @@ __device__ __forceinline__ void build_qsums(const float* A, float* qbuf, const i
       const int hp = t & 0xff, hm = (t >> 8) & 0xff;
       const float rp = A[hp], rm = A[hm], ip = A[NH + hp];
       const float im = __int_as_float(__float_as_int(A[NH + hm]) ^ (unsigned(t >> 16) << 31));
-      reinterpret_cast<float4*>(qbuf)[j + 16 * r] = make_float4(rp + rm, rp - rm, ip + im, ip - im);
+      reinterpret_cast<float4*>(qbuf)[j + G * r] = make_float4(rp + rm, rp - rm, ip + im, ip - im);
     }
   }
   if (j <= K) {

@@ -154,10 +154,14 @@ __host__ __device__ constexpr int spec_tile_w(int M, int Mz) {
 // kernel; the result is cached per (kernel, device, threads, smem), so the
 // attribute call and the occupancy query run once rather than every frame.
 struct ResidentShape { int nsm, per_sm; };
-cudaError_t resident_shape_of(const void* kernel, int threads, size_t smem, ResidentShape* out);
+// carveout >= 0: also set the kernel's preferred shared-memory carveout (percent
+// of the unified L1/shared storage), once per kernel and device.
+cudaError_t resident_shape_of(const void* kernel, int threads, size_t smem, ResidentShape* out,
+                              int carveout = -1);
 template <typename F>
-inline cudaError_t resident_shape(F* kernel, int threads, size_t smem, ResidentShape* out) {
-  return resident_shape_of(reinterpret_cast<const void*>(kernel), threads, smem, out);
+inline cudaError_t resident_shape(F* kernel, int threads, size_t smem, ResidentShape* out,
+                                  int carveout = -1) {
+  return resident_shape_of(reinterpret_cast<const void*>(kernel), threads, smem, out, carveout);
 }
 
 // launchers (return cudaError_t of the launch)

@@ -13,140 +13,158 @@
 // point of the largest R (v = l/lz, lz = 1); ties go to the lowest flat
 // index iy*L + ix.
 //
-// Mapping: a warp works on two pixels, one per half-warp.  Stage 1: lane j
-// owns ly = +-l_j (twiddles for its ly in registers) and reads the pixel's
-// Q sums from shared memory by broadcast.  Stage 2: lane j owns lx = +-l_j
-// and reads T(., ly) by broadcast, two ly rows per 16-byte load.  The
-// (cos, sin) x (re, im) products run as packed FP32x2 FMAs, each component
-// rounded exactly as fmaf.
+// Mapping: a warp works on four pixels, one per 8-lane group, and lane j owns
+// two grid values l_j and l_{j+8} (twiddles for both in registers), so every
+// broadcast shared-memory load feeds four packed FMAs.  Stage 1: lane j
+// computes T(kx, +-ly) for its two ly from the pixel's Q sums.  Stage 2: lane
+// j computes R(+-lx, ly) for its two lx, reading T(., ly) two ly rows per
+// 16-byte load.  The (cos, sin) x (re, im) products run as packed FP32x2 FMAs,
+// each component rounded exactly as fmaf, in the same order as ac::exact_R.
 #include "ac_common.cuh"
 #include "common.cuh"
 
 namespace wh {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kHalf = 16;   // lanes per pixel; the grid half-length (L+1)/2 must fit
+constexpr int kWarps4 = 4;
+constexpr int kGrp = 8;       // lanes per pixel; each owns two grid values, so (L+1)/2 <= 16
 
-template <int M>
-struct AcSmem {
-  static constexpr int kQ = ac::Geo<M>::QN;
-  static constexpr int kPad = ac::Geo<M>::KP;
-};
-
-// LP: row stride of the T buffer (even, >= L): 26 covers the common grids up
-// to L = 25 and lets three blocks share an SM; 32 covers L <= 31.
 template <int M, bool RS, int LP>
-__global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArgs a) {
-  constexpr int K = (M - 1) / 2;
-  constexpr int QN = AcSmem<M>::kQ, KP = AcSmem<M>::kPad;
+__global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrArgs a) {
+  using GE = ac::Geo<M>;
+  constexpr int K = GE::K, KP = GE::KP;
+  constexpr int QS = GE::QN + 4;                // Q-sum stride: the four groups' broadcasts in distinct banks
+  constexpr int TS = (K + 1) * LP + 2;          // T stride (float2): likewise
   const int L = a.L, Lh = (L + 1) / 2, gc = (L - 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int half = lane >> 4, j = lane & 15;
-  const int hw = wid * 2 + half;                        // half-warp (pixel slot) in the block
+  const int grp = lane >> 3, j = lane & 7;
+  const int slot = wid * 4 + grp;               // pixel slot in the block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sbase = reinterpret_cast<float*>(smem_raw);
-  float* abuf = sbase + hw * 2 * KP;                                                    // [2][KP]
-  float* qbuf = sbase + kWarps * 2 * 2 * KP + hw * QN;                                  // [QN]
-  constexpr int Lp = LP;          // row stride (>= L, even: rows gy, gy+1 load as one float4)
-  // per half-warp T buffer, padded by 64 bytes so the two half-warps' broadcast
-  // loads fall in different shared-memory banks
-  constexpr int TS = (K + 1) * Lp + 8;
-  float2* tbuf = reinterpret_cast<float2*>(sbase + kWarps * 2 * (2 * KP + QN)) + hw * TS;   // [K+1][Lp]
-  // lane-owned twiddles (cos, sin)(2pi k l_j / M), k = 1..K, l_j = j-th grid value >= 0
-  float2 cs[K];
-  const bool act = j < Lh;
+  constexpr int NSLOT = kWarps4 * 4;
+  // one state-row buffer per pixel slot: the next pixel's row is fetched into
+  // it as soon as the Q sums of this one are built (it lands during the stages)
+  float* abuf = sbase + slot * KP;                                              // [KP]
+  float* qbuf = sbase + NSLOT * KP + slot * QS;                                 // [QN]
+  float2* tbuf = reinterpret_cast<float2*>(sbase + NSLOT * (KP + QS)) + slot * TS;   // [K+1][LP]
+  const bool act0 = j < Lh, act1 = j + kGrp < Lh;
+  const int l0 = j, l1 = j + kGrp;
+  float2 c0[K], c1[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) cs[k] = act ? a.tab_x[(gc + j) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
-  constexpr int QIT = (ac::Geo<M>::NE + kHalf - 1) / kHalf;
+  for (int k = 0; k < K; ++k) {
+    c0[k] = act0 ? a.tab_x[(gc + l0) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
+    c1[k] = act1 ? a.tab_x[(gc + l1) * (K + 1) + k + 1] : make_float2(0.f, 0.f);
+  }
+  constexpr int QIT = (GE::NE + kGrp - 1) / kGrp;
   int qoff[QIT];
-  ac::qsum_offsets<M, QIT>(j, qoff);
+  ac::qsum_offsets<M, QIT, kGrp>(j, qoff);
   const float invL = 1.0f / float(L);
   const long long npix = a.pix_list ? (long long)*a.n_list : (long long)a.H * a.W;
-  const long long stride = (long long)gridDim.x * kWarps * 2;
-  auto pixel_of = [&](long long b) -> long long {
-    return a.pix_list ? (long long)a.pix_list[b] : b;
+  const long long stride = (long long)gridDim.x * NSLOT;
+  auto pixel_of = [&](long long b) -> long long { return a.pix_list ? (long long)a.pix_list[b] : b; };
+  auto prefetch = [&](long long b) {
+    ac::prefetch_row<M, kGrp>(abuf, a.Astate + (b < npix ? pixel_of(b) : 0) * KP, j, b < npix);
   };
-  // the state row of this half-warp's pixel at b -> abuf slot (16-byte copies)
-  auto prefetch = [&](long long b, int slot) {
-    ac::prefetch_row<M>(abuf + slot * KP, a.Astate + (b < npix ? pixel_of(b) : 0) * KP, j, b < npix);
-  };
-  long long base = ((long long)blockIdx.x * kWarps + wid) * 2;
-  prefetch(base + half, 0);
-  for (int it = 0; base < npix; base += stride, ++it) {
-    const bool valid = base + half < npix;
-    const long long pix = valid ? pixel_of(base + half) : 0;
+  long long base = ((long long)blockIdx.x * kWarps4 + wid) * 4;
+  prefetch(base + grp);
+  for (; base < npix; base += stride) {
+    const bool valid = base + grp < npix;
+    const long long pix = valid ? pixel_of(base + grp) : 0;
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    prefetch(base + stride + half, (it + 1) & 1);
-    // ---- Q sums of this half-warp's pixel ----------------------------------
-    if (valid) ac::build_qsums<M, QIT>(abuf + (it & 1) * KP, qbuf, qoff, j);
-    __syncwarp();
-    // ---- stage 1: T(kx, +-ly_j) ---------------------------------------------
-    if (valid && act) {
+    if (valid) ac::build_qsums<M, QIT, kGrp>(abuf, qbuf, qoff, j);
+    __syncwarp();                       // every lane's reads of abuf are done
+    prefetch(base + stride + grp);
+    // ---- stage 1: T(kx, +-ly) for ly = l_j, l_{j+8} ---------------------------
+    if (valid && act0) {
       const float4* q4 = reinterpret_cast<const float4*>(qbuf);
       const float2* q0 = reinterpret_cast<const float2*>(qbuf + 4 * (K + 1) * K);
 #pragma unroll 2
       for (int kx = 0; kx <= K; ++kx) {
         const float2 z = q0[kx];
-        float2 ac = make_float2(z.x, 0.f);   // (a, c)
-        float2 db = make_float2(z.y, 0.f);   // (d, b)
+        float2 ac0 = make_float2(z.x, 0.f), db0 = make_float2(z.y, 0.f);
+        float2 ac1 = ac0, db1 = db0;
 #pragma unroll
         for (int ky = 0; ky < K; ++ky) {
           const float4 q = q4[kx * K + ky];
-          ac = __ffma2_rn(make_float2(q.x, q.y), cs[ky], ac);
-          db = __ffma2_rn(make_float2(q.z, q.w), cs[ky], db);
+          ac0 = __ffma2_rn(make_float2(q.x, q.y), c0[ky], ac0);
+          db0 = __ffma2_rn(make_float2(q.z, q.w), c0[ky], db0);
+          ac1 = __ffma2_rn(make_float2(q.x, q.y), c1[ky], ac1);
+          db1 = __ffma2_rn(make_float2(q.z, q.w), c1[ky], db1);
         }
-        tbuf[kx * Lp + gc + j] = make_float2(ac.x - db.y, ac.y + db.x);
-        tbuf[kx * Lp + gc - j] = make_float2(ac.x + db.y, db.x - ac.y);
+        tbuf[kx * LP + gc + l0] = make_float2(ac0.x - db0.y, ac0.y + db0.x);
+        tbuf[kx * LP + gc - l0] = make_float2(ac0.x + db0.y, db0.x - ac0.y);
+        if (act1) {
+          tbuf[kx * LP + gc + l1] = make_float2(ac1.x - db1.y, ac1.y + db1.x);
+          tbuf[kx * LP + gc - l1] = make_float2(ac1.x + db1.y, db1.x - ac1.y);
+        }
       }
     }
     __syncwarp();
-    // ---- stage 2: R(+-lx_j, ly) and argmax ------------------------------------
+    // ---- stage 2: R(+-lx, ly) for lx = l_j, l_{j+8}, and the argmax -----------
     // R(+lx) = t0 + 2(v1 - v2), R(-lx) = t0 + 2(v1 + v2); their larger one is
-    // exactly t0 + 2(v1 + |v2|) (the same rounded operations).  Candidates reach
-    // this lane in increasing flat index (R(-lx) before R(+lx), row by row), so
-    // the first row reaching the maximum is kept and resolved at the end.
+    // exactly t0 + 2(v1 + |v2|) (the same rounded operations).  Per owned value
+    // the rows arrive in increasing flat index, so the first row reaching the
+    // value's maximum is kept and its -lx / +lx resolved at the end; values and
+    // lanes then combine by (largest R, lowest flat index).
     float best = -INFINITY;
     int bidx = 0x7fffffff;
-    if (valid && act) {
-      int bgy = 0;
-      auto row_v = [&](int gy) {
+    if (valid && act0) {
+      float b0 = -INFINITY, b1 = -INFINITY;
+      int g0 = 0, g1 = 0;
+      auto row_v = [&](const float2 (&cs)[K], int gy) {
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int kx = 1; kx <= K; ++kx) v = __ffma2_rn(cs[kx - 1], tbuf[kx * Lp + gy], v);
+        for (int kx = 1; kx <= K; ++kx) v = __ffma2_rn(cs[kx - 1], tbuf[kx * LP + gy], v);
         return v;
       };
-      auto take = [&](float r0, float2 v, int gy) {
+      auto take = [&](float r0, float2 v, int gy, int l, float& bb, int& bg) {
         if (RS) {
-          a.rs_out[pix * (L * L) + gy * L + gc + j] = fmaf(2.f, v.x - v.y, r0);
-          if (j) a.rs_out[pix * (L * L) + gy * L + gc - j] = fmaf(2.f, v.x + v.y, r0);
+          a.rs_out[pix * (L * L) + gy * L + gc + l] = fmaf(2.f, v.x - v.y, r0);
+          if (l) a.rs_out[pix * (L * L) + gy * L + gc - l] = fmaf(2.f, v.x + v.y, r0);
         }
         const float m = fmaf(2.f, v.x + fabsf(v.y), r0);
-        if (m > best) { best = m; bgy = gy; }
+        if (m > bb) { bb = m; bg = gy; }
       };
       int gy = 0;
       for (; gy + 1 < L; gy += 2) {
-        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+        float2 v00 = make_float2(0.f, 0.f), v01 = v00, v10 = v00, v11 = v00;
 #pragma unroll
         for (int kx = 1; kx <= K; ++kx) {
-          const float4 t = *reinterpret_cast<const float4*>(tbuf + kx * Lp + gy);
-          v0 = __ffma2_rn(cs[kx - 1], make_float2(t.x, t.y), v0);
-          v1 = __ffma2_rn(cs[kx - 1], make_float2(t.z, t.w), v1);
+          const float4 t = *reinterpret_cast<const float4*>(tbuf + kx * LP + gy);
+          v00 = __ffma2_rn(c0[kx - 1], make_float2(t.x, t.y), v00);
+          v01 = __ffma2_rn(c0[kx - 1], make_float2(t.z, t.w), v01);
+          v10 = __ffma2_rn(c1[kx - 1], make_float2(t.x, t.y), v10);
+          v11 = __ffma2_rn(c1[kx - 1], make_float2(t.z, t.w), v11);
         }
         const float4 t0 = *reinterpret_cast<const float4*>(tbuf + gy);
-        take(t0.x, v0, gy);
-        take(t0.z, v1, gy + 1);
+        take(t0.x, v00, gy, l0, b0, g0);
+        take(t0.z, v01, gy + 1, l0, b0, g0);
+        if (act1) {
+          take(t0.x, v10, gy, l1, b1, g1);
+          take(t0.z, v11, gy + 1, l1, b1, g1);
+        }
       }
-      if (gy < L) take(tbuf[gy].x, row_v(gy), gy);
-      // which of R(-lx), R(+lx) of the best row holds the maximum (-lx first)
-      const float2 v = row_v(bgy);
-      const float r0 = tbuf[bgy].x;
-      const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
-      bidx = bgy * L + (rm >= rp ? gc - j : gc + j);
+      if (gy < L) {
+        take(tbuf[gy].x, row_v(c0, gy), gy, l0, b0, g0);
+        if (act1) take(tbuf[gy].x, row_v(c1, gy), gy, l1, b1, g1);
+      }
+      // resolve -lx / +lx within each value's best row (-lx has the lower index)
+      auto resolve = [&](const float2 (&cs)[K], int bg, int l) {
+        const float2 v = row_v(cs, bg);
+        const float r0 = tbuf[bg].x;
+        const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
+        return bg * L + (rm >= rp ? gc - l : gc + l);
+      };
+      best = b0;
+      bidx = resolve(c0, g0, l0);
+      if (act1) {
+        const int i1 = resolve(c1, g1, l1);
+        if (b1 > best || (b1 == best && i1 < bidx)) { best = b1; bidx = i1; }
+      }
     }
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) {
+    for (int off = 4; off > 0; off >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, off);
       const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
       if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
@@ -164,33 +182,34 @@ __global__ void __launch_bounds__(kWarps * 32) autocorr_kernel(const AutocorrArg
 
 template <int M, int LP>
 cudaError_t launch_mp(const AutocorrArgs& a, cudaStream_t st) {
-  constexpr int K = (M - 1) / 2;
-  const size_t smem = sizeof(float) * size_t(kWarps) * 2 * (2 * AcSmem<M>::kPad + AcSmem<M>::kQ) +
-                      sizeof(float2) * size_t(kWarps) * 2 * ((K + 1) * LP + 8);
-  const long long npix = (long long)a.H * a.W;
+  using GE = ac::Geo<M>;
+  constexpr int K = GE::K, NSLOT = kWarps4 * 4;
+  const size_t smem = sizeof(float) * size_t(NSLOT) * (GE::KP + GE::QN + 4) +
+                      sizeof(float2) * size_t(NSLOT) * ((K + 1) * LP + 2);
+  const long long npix = (long long)a.H * a.W;   // a pixel list is at most this long
   auto kern = a.rs_out ? autocorr_kernel<M, true, LP> : autocorr_kernel<M, false, LP>;
-  // one resident wave (blocks per SM from the occupancy of this shape), the
-  // pixel pairs strided over it, so no partial last wave idles SMs
+  // all of the SM's unified L1/shared storage as shared memory: four blocks
+  // (16 warps) fit at M = 15, L <= 25 (the kernel re-reads nothing through L1)
   ResidentShape rs{};
-  cudaError_t e = resident_shape(kern, kWarps * 32, smem, &rs);
+  cudaError_t e = resident_shape(kern, kWarps4 * 32, smem, &rs, 100);
   if (e != cudaSuccess) return e;
   const int nsm = rs.nsm, per_sm = rs.per_sm < 1 ? 1 : rs.per_sm;
-  long long blocks = (npix + 2 * kWarps - 1) / (2 * kWarps);
+  long long blocks = (npix + NSLOT - 1) / NSLOT;
   if (blocks > (long long)nsm * per_sm) blocks = (long long)nsm * per_sm;
-  kern<<<unsigned(blocks), kWarps * 32, smem, st>>>(a);
+  kern<<<unsigned(blocks), kWarps4 * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int M>
 cudaError_t launch_m(const AutocorrArgs& a, cudaStream_t st) {
-  if (a.kpad != AcSmem<M>::kPad) return cudaErrorInvalidValue;
-  return a.L <= 25 ? launch_mp<M, 26>(a, st) : launch_mp<M, 2 * kHalf>(a, st);
+  if (a.kpad != ac::Geo<M>::KP) return cudaErrorInvalidValue;
+  return a.L <= 25 ? launch_mp<M, 26>(a, st) : launch_mp<M, 32>(a, st);
 }
 
 }  // namespace
 
 cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st) {
-  if ((a.L + 1) / 2 > kHalf || (a.L % 2) == 0) return cudaErrorInvalidValue;
+  if ((a.L + 1) / 2 > 2 * kGrp || (a.L % 2) == 0) return cudaErrorInvalidValue;
   switch (a.M) {
     case 5: return launch_m<5>(a, st);
     case 7: return launch_m<7>(a, st);

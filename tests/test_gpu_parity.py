@@ -90,6 +90,14 @@ def test_parity_ragged_odd_even_orders(M, Mz, H, W):
     _compare(sc.frames, M, Mz, 1.5, 0.5, spec_frames=(Mz - 1, 11))
 
 
+@pytest.mark.parametrize("M,Mz,vmax,step", [(9, 4, 3.75, 0.25), (5, 6, 1.5, 0.1)])
+def test_parity_widest_grid(M, Mz, vmax, step):
+    """L = 31, the widest grid the search takes: every lane of a pixel's group
+    owns two grid values, and the T rows use the wider stride."""
+    sc = scenes.small_scene(T=10, H=21, W=38, seed=M + 100 * Mz, vx=1.2, vy=-0.9, tex_size=128)
+    _compare(sc.frames, M, Mz, vmax, step, spec_frames=(9,))
+
+
 def test_parity_frame_smaller_than_window():
     sc = scenes.small_scene(T=8, H=5, W=7, seed=3, tex_size=64)
     _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(7,), check_vel_frac=False)
