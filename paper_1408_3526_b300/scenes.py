@@ -245,32 +245,35 @@ def training_scene_set(n_scenes, T, H, W, seed0=100, vlim=1.75, tex_size=2048, n
         yield frames, (float(vx), float(vy))
 
 
-def paper_sim_scene(T=32, H=64, W=64, seed=5):
-    """The paper's own simulation recipe (Sec. 3), re-generated from its text.
+def paper_sim_scene(T=32, H=64, W=64, seed=5, components=25, fmax=2 / 9, magnitude=0.1, dc=10.0,
+                    v_clt=(1.625, 0.625), v_tgt=(-0.625, -0.375), tgt_peak=1.0, psf_sigma=1.0,
+                    truncation=0.1, noise_sigma=0.1):
+    """The paper's own simulation recipe (Sec. 3), re-generated from its text
+    (the defaults are the values it prints).
 
-    25 sinusoidal components with spatial frequencies U[-2/9, 2/9] cycles/px,
-    random phase, magnitude 0.1, DC 10, translating at (1.625, 0.625)
-    px/frame.  One occluding target: Gaussian PSF, sigma 1 px, peak 1.0,
-    truncated below 0.1, velocity (-0.625, -0.375), centred in the last frame.
-    Zero-mean Gaussian noise of sigma 0.1.
+    `components` sinusoids with spatial frequencies U[-fmax, fmax] cycles/px,
+    random phase, the given magnitude, plus the DC offset, translating at
+    v_clt px/frame.  One occluding target: Gaussian PSF of psf_sigma px and
+    peak tgt_peak, truncated below `truncation`, velocity v_tgt, centred in
+    the last frame.  Zero-mean Gaussian noise of noise_sigma.
     """
     rng = np.random.default_rng(seed)
-    comps = [(rng.uniform(-2 / 9, 2 / 9), rng.uniform(-2 / 9, 2 / 9), 0.1,
-              rng.uniform(0, 2 * np.pi)) for _ in range(25)]
-    vx, vy = 1.625, 0.625
-    bg = sinusoid_scene(H, W, T, comps, vx, vy, dc=10.0)
-    tvx, tvy = -0.625, -0.375
+    comps = [(rng.uniform(-fmax, fmax), rng.uniform(-fmax, fmax), magnitude,
+              rng.uniform(0, 2 * np.pi)) for _ in range(components)]
+    vx, vy = v_clt
+    bg = sinusoid_scene(H, W, T, comps, vx, vy, dc=dc)
+    tvx, tvy = v_tgt
     cx_end, cy_end = (W - 1) / 2.0, (H - 1) / 2.0
     py, px = np.mgrid[0:H, 0:W].astype(np.float64)
     frames = np.empty((T, H, W), np.float32)
     for t in range(T):
         cx = cx_end + tvx * (t - (T - 1))
         cy = cy_end + tvy * (t - (T - 1))
-        psf = np.exp(-((px - cx) ** 2 + (py - cy) ** 2) / 2.0)
-        img = np.where(psf >= 0.1, psf, bg[t])       # the target occludes
-        img = img + 0.1 * rng.standard_normal((H, W))
+        psf = tgt_peak * np.exp(-((px - cx) ** 2 + (py - cy) ** 2) / (2.0 * psf_sigma ** 2))
+        img = np.where(psf >= truncation, psf, bg[t])       # the target occludes
+        img = img + noise_sigma * rng.standard_normal((H, W))
         frames[t] = img
     targets = [dict(x0=cx_end + tvx * (-(T - 1)), y0=cy_end + tvy * (-(T - 1)), vx=tvx,
-                    vy=tvy, sigma=1.0, amp=1.0)]
+                    vy=tvy, sigma=psf_sigma, amp=tgt_peak)]
     return Scene(frames, np.full((H, W), vx, np.float32), np.full((H, W), vy, np.float32),
-                 targets, 0.1, 0.1)
+                 targets, noise_sigma, magnitude)
