@@ -20,6 +20,8 @@
 // j computes R(+-lx, ly) for its two lx, reading T(., ly) two ly rows per
 // 16-byte load.  The (cos, sin) x (re, im) products run as packed FP32x2 FMAs,
 // each component rounded exactly as fmaf, in the same order as ac::exact_R.
+// Stage 2 evaluates only the rows whose upper bound reaches the value of the
+// most promising row (exact pruning, see the row bounds below).
 #include "ac_common.cuh"
 #include "common.cuh"
 
@@ -27,6 +29,13 @@ namespace wh {
 namespace {
 
 constexpr int kWarps4 = 4;
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 constexpr int kGrp = 8;       // lanes per pixel; each owns two grid values, so (L+1)/2 <= 16
 
 template <int M, bool RS, int LP>
@@ -107,18 +116,71 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
     // the rows arrive in increasing flat index, so the first row reaching the
     // value's maximum is kept and its -lx / +lx resolved at the end; values and
     // lanes then combine by (largest R, lowest flat index).
+    auto row_v = [&](const float2 (&cs)[K], int gy) {
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int kx = 1; kx <= K; ++kx) v = __ffma2_rn(cs[kx - 1], tbuf[kx * LP + gy], v);
+      return v;
+    };
+    auto mval = [](float r0, float2 v) { return fmaf(2.f, v.x + fabsf(v.y), r0); };
+    // Row bounds: R(lx, ly) <= t0 + 2 sum_kx |T(kx, ly)| (Cauchy-Schwarz per kx,
+    // |(cos, sin)| = 1).  The relative margin 2^-12 covers every FP32 rounding
+    // of the evaluated R (~1e-6) and of the bound, whose square roots are the
+    // hardware approximation (relative error ~2^-22).  The row with the largest
+    // bound is evaluated first; a row whose bound is below that value holds no
+    // maximum (nor a tie), so only the row pairs with a row reaching it are
+    // evaluated, in increasing order, and the argmax is exactly that of the
+    // full evaluation.
+    constexpr float kUbRel = 1.0f / 4096.0f;
+    const unsigned all_pairs = (1u << ((L + 1) / 2)) - 1u;
+    unsigned pairs = all_pairs;
+    if (!RS) {
+      float u[4];
+      float um = -INFINITY;
+      int ur = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int ly = j + kGrp * t;
+        u[t] = -INFINITY;
+        if (valid && ly < L) {
+          float sa = 0.f;
+#pragma unroll
+          for (int kx = 1; kx <= K; ++kx) {
+            const float2 tv = tbuf[kx * LP + ly];
+            sa += sqrt_approx(fmaf(tv.x, tv.x, tv.y * tv.y));
+          }
+          const float t0 = tbuf[ly].x;
+          u[t] = fmaf(2.f * sa, 1.f + kUbRel, fmaf(kUbRel, fabsf(t0), t0));
+          if (u[t] > um) { um = u[t]; ur = ly; }
+        }
+      }
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) {
+        const float ou = __shfl_xor_sync(0xffffffffu, um, off);
+        const int orow = __shfl_xor_sync(0xffffffffu, ur, off);
+        if (ou > um || (ou == um && orow < ur)) { um = ou; ur = orow; }
+      }
+      float seed = -INFINITY;
+      if (valid && act0) {
+        const float r0 = tbuf[ur].x;
+        seed = mval(r0, row_v(c0, ur));
+        if (act1) seed = fmaxf(seed, mval(r0, row_v(c1, ur)));
+      }
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) seed = fmaxf(seed, __shfl_xor_sync(0xffffffffu, seed, off));
+      unsigned need = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (u[t] >= seed) need |= 1u << ((j + kGrp * t) >> 1);
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) need |= __shfl_xor_sync(0xffffffffu, need, off);
+      if (isfinite(seed)) pairs = need & all_pairs;
+    }
     float best = -INFINITY;
     int bidx = 0x7fffffff;
     if (valid && act0) {
       float b0 = -INFINITY, b1 = -INFINITY;
       int g0 = 0, g1 = 0;
-      auto row_v = [&](const float2 (&cs)[K], int gy) {
-        float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int kx = 1; kx <= K; ++kx) v = __ffma2_rn(cs[kx - 1], tbuf[kx * LP + gy], v);
-        return v;
-      };
-      auto mval = [](float r0, float2 v) { return fmaf(2.f, v.x + fabsf(v.y), r0); };
       auto take = [&](float r0, float2 v, int gy, int l, float& bb, int& bg) {
         if (RS) {
           a.rs_out[pix * (L * L) + gy * L + gc + l] = fmaf(2.f, v.x - v.y, r0);
@@ -127,8 +189,13 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
         const float m = fmaf(2.f, v.x + fabsf(v.y), r0);
         if (m > bb) { bb = m; bg = gy; }
       };
-      int gy = 0;
-      for (; gy + 1 < L; gy += 2) {
+      for (unsigned pm = pairs; pm; pm &= pm - 1) {
+        const int gy = 2 * (__ffs(pm) - 1);
+        if (gy + 1 >= L) {                 // the last row of an odd grid
+          take(tbuf[gy].x, row_v(c0, gy), gy, l0, b0, g0);
+          if (act1) take(tbuf[gy].x, row_v(c1, gy), gy, l1, b1, g1);
+          continue;
+        }
         float2 v00 = make_float2(0.f, 0.f), v01 = v00, v10 = v00, v11 = v00;
 #pragma unroll
         for (int kx = 1; kx <= K; ++kx) {
@@ -155,10 +222,6 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
             if (m1 > b1) { b1 = m1; g1 = gy; }
           }
         }
-      }
-      if (gy < L) {
-        take(tbuf[gy].x, row_v(c0, gy), gy, l0, b0, g0);
-        if (act1) take(tbuf[gy].x, row_v(c1, gy), gy, l1, b1, g1);
       }
       // resolve -lx / +lx within each value's best row (-lx has the lower index)
       auto resolve = [&](const float2 (&cs)[K], float bb, int bg, int l) {
