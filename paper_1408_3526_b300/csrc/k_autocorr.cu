@@ -85,9 +85,18 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
     __syncwarp();                       // every lane's reads of abuf are done
     prefetch(base + stride + grp);
     // ---- stage 1: T(kx, +-ly) for ly = l_j, l_{j+8} ---------------------------
+    // Each lane also accumulates, for its four rows gc +- l_j, gc +- l_{j+8},
+    // t0 = Re T(0, ly) and sum_{kx>=1} |T(kx, ly)| for the row bounds below.
+    float rt0[4], rsa[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) { rt0[t] = 0.f; rsa[t] = 0.f; }
     if (valid && act0) {
       const float4* q4 = reinterpret_cast<const float4*>(qbuf);
       const float2* q0 = reinterpret_cast<const float2*>(qbuf + 4 * (K + 1) * K);
+      auto acc = [&](int kx, int t, float2 tv) {
+        if (kx == 0) rt0[t] = tv.x;
+        else if (!RS) rsa[t] += sqrt_approx(fmaf(tv.x, tv.x, tv.y * tv.y));
+      };
 #pragma unroll 2
       for (int kx = 0; kx <= K; ++kx) {
         const float2 z = q0[kx];
@@ -101,11 +110,19 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
           ac1 = __ffma2_rn(make_float2(q.x, q.y), c1[ky], ac1);
           db1 = __ffma2_rn(make_float2(q.z, q.w), c1[ky], db1);
         }
-        tbuf[kx * LP + gc + l0] = make_float2(ac0.x - db0.y, ac0.y + db0.x);
-        tbuf[kx * LP + gc - l0] = make_float2(ac0.x + db0.y, db0.x - ac0.y);
+        const float2 tp0 = make_float2(ac0.x - db0.y, ac0.y + db0.x);
+        const float2 tm0 = make_float2(ac0.x + db0.y, db0.x - ac0.y);
+        tbuf[kx * LP + gc + l0] = tp0;
+        tbuf[kx * LP + gc - l0] = tm0;
+        acc(kx, 0, tp0);
+        acc(kx, 1, tm0);
         if (act1) {
-          tbuf[kx * LP + gc + l1] = make_float2(ac1.x - db1.y, ac1.y + db1.x);
-          tbuf[kx * LP + gc - l1] = make_float2(ac1.x + db1.y, db1.x - ac1.y);
+          const float2 tp1 = make_float2(ac1.x - db1.y, ac1.y + db1.x);
+          const float2 tm1 = make_float2(ac1.x + db1.y, db1.x - ac1.y);
+          tbuf[kx * LP + gc + l1] = tp1;
+          tbuf[kx * LP + gc - l1] = tm1;
+          acc(kx, 2, tp1);
+          acc(kx, 3, tm1);
         }
       }
     }
@@ -135,24 +152,17 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
     const unsigned all_pairs = (1u << ((L + 1) / 2)) - 1u;
     unsigned pairs = all_pairs;
     if (!RS) {
+      // this lane's rows gc + l_j, gc - l_j, gc + l_{j+8}, gc - l_{j+8} (the
+      // second copy of row gc for l_j = 0 left out)
+      const int rows[4] = {gc + l0, gc - l0, gc + l1, gc - l1};
+      const bool own[4] = {valid && act0, valid && act0 && l0 > 0, valid && act1, valid && act1};
       float u[4];
       float um = -INFINITY;
       int ur = 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int ly = j + kGrp * t;
-        u[t] = -INFINITY;
-        if (valid && ly < L) {
-          float sa = 0.f;
-#pragma unroll
-          for (int kx = 1; kx <= K; ++kx) {
-            const float2 tv = tbuf[kx * LP + ly];
-            sa += sqrt_approx(fmaf(tv.x, tv.x, tv.y * tv.y));
-          }
-          const float t0 = tbuf[ly].x;
-          u[t] = fmaf(2.f * sa, 1.f + kUbRel, fmaf(kUbRel, fabsf(t0), t0));
-          if (u[t] > um) { um = u[t]; ur = ly; }
-        }
+        u[t] = own[t] ? fmaf(2.f * rsa[t], 1.f + kUbRel, fmaf(kUbRel, fabsf(rt0[t]), rt0[t])) : -INFINITY;
+        if (u[t] > um || (u[t] == um && own[t] && rows[t] < ur)) { um = u[t]; ur = rows[t]; }
       }
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) {
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
       unsigned need = 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (u[t] >= seed) need |= 1u << ((j + kGrp * t) >> 1);
+        if (own[t] && u[t] >= seed) need |= 1u << (rows[t] >> 1);
 #pragma unroll
       for (int off = 4; off > 0; off >>= 1) need |= __shfl_xor_sync(0xffffffffu, need, off);
       if (isfinite(seed)) pairs = need & all_pairs;
