@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
       auto resolve = [&](const float2 (&cs)[K], float bb, int bg, int l) {
         // without the dump the kept row pair's first row attaining the maximum
         // (a row past the pair can only be a later, tie-losing one)
-        if (!RS && bg + 1 < L && !(mval(tbuf[bg].x, row_v(cs, bg)) == bb)) ++bg;
+        if (!RS && bg + 1 < L && !(mval(tbuf[bg].x, row_v(cs, bg)) == bb) &&
+            mval(tbuf[bg + 1].x, row_v(cs, bg + 1)) == bb)
+          ++bg;
         const float2 v = row_v(cs, bg);
         const float r0 = tbuf[bg].x;
         const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
