@@ -243,8 +243,12 @@ __device__ __forceinline__ void observer_hann(const float* pa, float2 (&T)[SG<M,
   }
 }
 
-template <int M, int MZ, bool DUMP>
+// MODE 0: the plain path (no dump, no features, both compiled out); 1: debug
+// dump of the windowed spectrum and power (features if requested); 2: the
+// learned estimator's features.
+template <int M, int MZ, int MODE>
 __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const SpecArgs a) {
+  constexpr bool DUMP = MODE == 1;
   using G = SG<M, MZ>;
   constexpr int K = G::K, J = G::J, NPL = G::NPL, NCHY = G::NCHY;
   constexpr int TW = G::TW, RW = G::RW, NTHR = G::NTHR, PS = G::PS, KPAD = G::KPAD;
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   int* fgs = reinterpret_cast<int*>(smem_raw + G::O_FGS);
   float* fpart = reinterpret_cast<float*>(smem_raw + G::O_FPART);
   float* ftot = reinterpret_cast<float*>(smem_raw + G::O_FTOT);
-  const bool feat = a.feat != nullptr;
+  const bool feat = MODE != 0 && a.feat != nullptr;
   if (feat)
     for (int i = tid; i < G::NBINS; i += NTHR) fgs[i] = a.feat_gather[i];
 
@@ -670,8 +674,8 @@ template <int M, int MZ>
 cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   using G = SG<M, MZ>;
   if (a.tw != G::TW || a.kpad != G::KPAD) return cudaErrorInvalidValue;
-  const bool dump = a.dump_win != nullptr;
-  auto kern = dump ? spectrum_kernel<M, MZ, true> : spectrum_kernel<M, MZ, false>;
+  auto kern = a.dump_win ? spectrum_kernel<M, MZ, 1>
+                         : (a.feat ? spectrum_kernel<M, MZ, 2> : spectrum_kernel<M, MZ, 0>);
   ResidentShape rs{};
   cudaError_t e = resident_shape(kern, G::NTHR, G::SMEM, &rs);
   if (e != cudaSuccess) return e;
