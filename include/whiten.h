@@ -278,6 +278,12 @@ int wh_read_spectrum(wh_stream *s, int kind, void *out, int is_device);
  * Smoothed autocorrelation R'(l; n) of the last frame on the velocity grid,
  * float32 [h][w][L][L] (ly slowest), recomputed from the stream's smoothed
  * spectral state (Sec. 2: R is linear in P).  For tests and diagnostics.
+ * The recomputation evaluates every grid value (the per-frame search skips
+ * rows that provably hold no maximum) and rewrites the velocity field of the
+ * last frame from it; the values are identical, so wh_read_velocity before
+ * and after compares the two searches.  The library allocates the H*W*L*L
+ * float buffer on first use and keeps it until the stream is destroyed.
+ * Errors: WH_ENOTREADY (no frame pushed), WH_EINVAL, WH_ENOMEM, WH_ECUDA.
  */
 int wh_read_autocorr(wh_stream *s, float *out, int is_device);
 

@@ -783,7 +783,13 @@ int wh_read_autocorr(wh_stream* s, float* out, int is_device) {
   { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
   if (s->t < 1) return WH_ENOTREADY;
   const size_t n = size_t(s->H) * s->W * s->L * s->L;
-  if (!s->d_rs) WH_CU(cudaMalloc((void**)&s->d_rs, sizeof(float) * n));
+  if (!s->d_rs) {
+    const cudaError_t me = cudaMalloc((void**)&s->d_rs, sizeof(float) * n);
+    if (me != cudaSuccess) {
+      s->d_rs = nullptr;
+      return me == cudaErrorMemoryAllocation ? WH_ENOMEM : set_cuda_err(me, "cudaMalloc");
+    }
+  }
   AutocorrArgs aa{};
   aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
   aa.vmax = float(s->vmax); aa.vstep = float(s->vstep); aa.Astate = s->Astate;
