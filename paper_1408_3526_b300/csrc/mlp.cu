@@ -239,6 +239,27 @@ int forward_impl(wh_mlp* m, const void* x, int ldx, int n, bool train) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+namespace wh {
+// Forward pass enqueued on `st` (the caller's stream) instead of the network's
+// own: the whitening stream's learned search runs it between its spectrum and
+// selection kernels, which must see its input and output in stream order.
+// The network's buffers are shared, so one network serves one caller at a time.
+int mlp_forward_on(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy, cudaStream_t st) {
+  if (!m || !x || n < 1 || ldx < m->n_in || (ldx % 8)) return WH_EINVAL;
+  const cudaStream_t own = m->st;
+  m->st = st;
+  int rc = ensure_cap(m, n, false);
+  if (rc == WH_OK) rc = forward_impl(m, x, ldx, n, false);
+  if (rc == WH_OK && y) {
+    const cudaError_t e = cudaMemcpy2DAsync(y, sizeof(float) * ldy, m->Y, sizeof(float) * m->o_pad,
+                                            sizeof(float) * m->n_out, n, cudaMemcpyDeviceToDevice, m->st);
+    if (e != cudaSuccess) rc = wh_cuda_fail(e, "mlp output copy");
+  }
+  m->st = own;
+  return rc;
+}
+}  // namespace wh
+
 extern "C" {
 
 int wh_mlp_create(int n_in, int h1, int h2, int n_out, unsigned long long seed, void* cuda_stream, wh_mlp** out) {
@@ -353,16 +374,8 @@ int wh_mlp_set_params(wh_mlp* m, const float* host, long long n) {
 int wh_mlp_get_grads(wh_mlp* m, float* host, long long n) { return params_io(m, host, n, true, true); }
 
 int wh_mlp_forward(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy) {
-  if (!m || !x || n < 1 || ldx < m->n_in || (ldx % 8)) return WH_EINVAL;
-  int rc = ensure_cap(m, n, false);
-  if (rc != WH_OK) return rc;
-  if ((rc = forward_impl(m, x, ldx, n, false)) != WH_OK) return rc;
-  if (y) {
-    const cudaError_t e = cudaMemcpy2DAsync(y, sizeof(float) * ldy, m->Y, sizeof(float) * m->o_pad,
-                                            sizeof(float) * m->n_out, n, cudaMemcpyDeviceToDevice, m->st);
-    if (e != cudaSuccess) return wh_cuda_fail(e, "mlp output copy");
-  }
-  return WH_OK;
+  if (!m) return WH_EINVAL;
+  return wh::mlp_forward_on(m, x, ldx, n, y, ldy, m->st);
 }
 
 int wh_mlp_train_step(wh_mlp* m, const void* x, int ldx, int n, const float* target, float vstep, float lr,

@@ -149,11 +149,15 @@ __global__ void learned_select_kernel(const float* y, int npix, float thr, float
 
 __global__ void accumulate_count_kernel(const int* n, long long* total) { *total += *n; }
 
-extern "C" int wh_mlp_forward(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy);
+namespace wh {
+int mlp_forward_on(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy, cudaStream_t st);
+}
 
 static int learned_search(wh_stream* s) {
   const int npix = s->H * s->W;
-  int rc = wh_mlp_forward(s->mlp, s->d_feat, s->feat_ld, npix, s->d_ymlp, 3);
+  // on the search's stream: the network reads the features this frame's
+  // spectrum kernel wrote and the selection below reads its output
+  int rc = wh::mlp_forward_on(s->mlp, s->d_feat, s->feat_ld, npix, s->d_ymlp, 3, s->st);
   if (rc != WH_OK) return rc;
   WH_CU(cudaMemsetAsync(s->d_nlist, 0, sizeof(int), s->st));
   learned_select_kernel<<<148 * 8, 256, 0, s->st>>>(s->d_ymlp, npix, s->conf_thr, float(s->vmax),
@@ -203,7 +207,7 @@ static void free_pipeline(wh_stream* s) {
   if (!s->pipeline) return;
   if (s->st_s) cudaStreamSynchronize(s->st_s);
   if (s->st_p) cudaStreamSynchronize(s->st_p);
-  for (cudaEvent_t e : {s->ev_user, s->ev_spec, s->ev_join, s->ev_pef[0], s->ev_pef[1]})
+  for (cudaEvent_t e : {s->ev_user, s->ev_spec, s->ev_join, s->ev_pef[0], s->ev_pef[1], s->ev_feat})
     if (e) cudaEventDestroy(e);
   if (s->st_s) cudaStreamDestroy(s->st_s);
   if (s->st_p) cudaStreamDestroy(s->st_p);
@@ -310,7 +314,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     alloc((void**)&s->Astate_alt, sizeof(float) * npix * s->kpad);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&s->ev_user, &s->ev_spec, &s->ev_join, &s->ev_pef[0], &s->ev_pef[1]})
+    for (cudaEvent_t* ev : {&s->ev_user, &s->ev_spec, &s->ev_join, &s->ev_pef[0], &s->ev_pef[1], &s->ev_feat})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   }
   alloc((void**)&s->frame, sizeof(float) * npix);
@@ -505,6 +509,9 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
   const cudaStream_t sp = s->pipeline ? s->st_p : s->st;
   const int k = int(s->t & 1);
   if (s->pipeline && s->pef_used[k]) WH_CU(cudaStreamWaitEvent(ss, s->ev_pef[k], 0));
+  // one feature buffer: with features on, the spectrum of this frame waits
+  // until the previous frame's learned search has read it (no overlap there)
+  if (s->pipeline && s->d_feat) WH_CU(cudaStreamWaitEvent(ss, s->ev_feat, 0));
   if (wait_spec) WH_CU(cudaStreamWaitEvent(ss, wait_spec, 0));
   cudaEvent_t* ev = nullptr;
   if (s->prof && s->ev_used + 4 <= 4 * 65536) {
@@ -563,6 +570,8 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
     aa.tab_y = s->d_taby; aa.tab_x = s->d_tabx; aa.pix_list = nullptr; aa.n_list = nullptr;
     if ((e = launch_autocorr(aa, sp)) != cudaSuccess) rc = set_cuda_err(e, "autocorrelation kernel");
   }
+  if (rc == WH_OK && s->pipeline && s->d_feat && (e = cudaEventRecord(s->ev_feat, sp)) != cudaSuccess)
+    rc = set_cuda_err(e, "cudaEventRecord");
   if (rc == WH_OK && ev && (e = cudaEventRecord(ev[2], sp)) != cudaSuccess) rc = set_cuda_err(e, "cudaEventRecord");
   if (rc == WH_OK) {
     PefArgs pa{};

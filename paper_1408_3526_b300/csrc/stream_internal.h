@@ -71,6 +71,7 @@ struct wh_stream {
   int pipeline;
   cudaStream_t st_s, st_p;
   cudaEvent_t ev_user, ev_spec, ev_join, ev_pef[2];
+  cudaEvent_t ev_feat;       // the search of the last frame has read the feature buffer
   int pef_used[2];
   int pipe_work;              // kernels were enqueued since the last join
   float* Astate_alt;

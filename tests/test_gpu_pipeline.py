@@ -84,3 +84,34 @@ def test_pipeline_unread_frames_then_async_push():
         for t in range(T // 2, T):
             assert np.array_equal(outs[t][1].numpy(), ref[t][0]), t
             assert np.array_equal(outs[t][0].numpy(), ref[t][1]), t
+
+
+@pytest.mark.parametrize("conf", [0.0, 0.8])
+def test_pipeline_learned_mode_identical_to_serial(conf):
+    """Learned velocity mode with the frame pipeline: the spectrum kernel of
+    frame t+1 writes the feature buffer that the network of frame t reads, so
+    it must wait for that search; frames are pushed back to back (no reads in
+    between) and the results must equal the serial stream's."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1408_3526_b300 import learned
+    from paper_1408_3526_b300.stream import WhitenStream
+    net = learned.MLP(M * M * MZ, 256, 128, 3, seed=3)
+    fr = scenes.config1_scene(T=T, H=H, W=W, seed=11).frames.astype(np.float32)
+    dev = torch.from_numpy(fr).cuda()
+    res = []
+    for pipeline in (False, True):
+        with WhitenStream(H, W, M, MZ, VMAX, VSTEP, pipeline=pipeline) as s:
+            assert s.lib.wh_stream_set_learned(s._s, net._m, conf) == 0
+            for t in range(T):
+                s.push(dev[t])
+            vx, vy, vi, _ = s.read_velocity()
+            w, _ = s.read_whitened()
+            nfr, nfb = C.c_longlong(), C.c_longlong()
+            assert s.lib.wh_stream_learned_stats(s._s, C.byref(nfr), C.byref(nfb)) == 0
+            res.append((vx, vy, vi, w, np.array([nfr.value, nfb.value])))
+    net.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
