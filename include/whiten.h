@@ -43,7 +43,8 @@ extern "C" {
 
 /* ---- status codes ------------------------------------------------------- */
 #define WH_OK         0
-#define WH_EINVAL    -1   /* bad argument: even or < 3 window, Mz < 2, grid step <= 0, h or w < 1, NULL */
+#define WH_EINVAL    -1   /* bad argument: even or < 3 window, Mz < 2, grid step <= 0, h or w < 1,
+                             h * w > 2^30, NULL */
 #define WH_ENOMEM    -2   /* device or host allocation failed */
 #define WH_EADMIT    -3   /* request exceeds the memory budget (serving admission) */
 #define WH_ENOTREADY -4   /* output not available yet (fewer than m'_z + 1 frames pushed) */
@@ -102,7 +103,7 @@ int wh_default_params(int window, int temporal_order, wh_params *p);
  * Create a stream: allocate its device state (observer bank, smoothed
  * autocorrelation basis, outputs) and build its tables (SDFT twiddles, Hann
  * taps, Eq. (8)/(2) filter weights per grid velocity, Eq. (10) basis).
- *   frame_h, frame_w   frame size (>= 1 each)
+ *   frame_h, frame_w   frame size (>= 1 each, frame_h * frame_w <= 2^30)
  *   window             spatial window M = 2K+1 (odd, 3..15)
  *   temporal_order     Mz, temporal bins / observer states (2..8)
  *   velocity_grid      search grid for the autocorrelation peak

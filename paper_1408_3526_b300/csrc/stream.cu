@@ -251,6 +251,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   if (!out) return WH_EINVAL;
   *out = nullptr;
   if (H < 1 || W < 1 || M < 3 || (M % 2) == 0 || M > kMaxM || Mz < 2 || Mz > kMaxMz) return WH_EINVAL;
+  if ((long long)H * W > kMaxPixels) return WH_EINVAL;   // pixel counts stay 32-bit in the kernels
   if (!(grid.step > 0.f) || !(grid.vmax >= 0.f)) return WH_EINVAL;
   const double Ld = 2.0 * grid.vmax / grid.step + 1.0;
   const int L = int(std::lround(Ld));

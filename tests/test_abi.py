@@ -59,6 +59,7 @@ def test_status_strings_and_defaults(lib):
     (64, 64, 9, 4, 2.0, 0.0),     # step <= 0
     (64, 64, 9, 4, 2.0, 0.3),     # vmax not a multiple of step
     (64, 64, 9, 4, 20.0, 0.25),   # grid longer than the kernels' limit
+    (40000, 40000, 9, 4, 2.0, 0.25),  # more than 2^30 pixels
 ])
 def test_create_rejects_bad_arguments_without_cuda(lib, args):
     h, w, M, Mz, vmax, step = args
