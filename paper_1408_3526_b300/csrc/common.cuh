@@ -19,7 +19,6 @@ namespace wh {
 constexpr int kMaxM = 15;
 constexpr int kMaxMz = 8;
 constexpr int kMaxL = 31;
-constexpr long long kMaxPixels = 1LL << 30;   // h * w (far beyond what fits in memory with the state)
 constexpr int kMaxPlanes = kMaxMz / 2 + 1;
 constexpr int kMaxChan = 2 * (kMaxM) + (kMaxPlanes) * kMaxM + kMaxPlanes;
 

@@ -246,6 +246,9 @@ int wh_default_params(int window, int temporal_order, wh_params* p) {
   return WH_OK;
 }
 
+// h * w limit (far beyond what fits in device memory with the per-pixel state)
+constexpr long long kMaxPixels = 1LL << 30;
+
 int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params* opt,
                      void* cuda_stream, wh_stream** out) {
   if (!out) return WH_EINVAL;
