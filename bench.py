@@ -214,20 +214,19 @@ def run_reference(args):
     frames = make_frames()
     o = oracle.Oracle(M, MZ, VMAX, VSTEP)
     cores = os.cpu_count() or 1
-    T = 6
-    # per-step sample: the largest crop whose K + W steps fit in about 90 s
-    # (the oracle's cost grows with the crop plus its (M - 1)-pixel halo)
-    crops = [(24, 32), (16, 24), (12, 16), (8, 12), (8, 8)]
-    t0 = time.perf_counter()
-    o.run(frames[:T], crop=(240, 300) + crops[0], nthreads=cores)
-    t_big = time.perf_counter() - t0
-    area = lambda c: (c[0] + M - 1) * (c[1] + M - 1)
-    h, w = crops[-1]
-    for c in crops:
-        if t_big * area(c) / area(crops[0]) * (args.steps + args.warmup) <= 90.0:
-            h, w = c
-            break
+    # per-step sample: a fixed 24x32 crop (the oracle also computes its (M - 1)-pixel
+    # halo, so the crop is not shrunk, which would bias the rate low) over the most
+    # frames, of 6, whose K + W steps fit in about 90 s; every frame costs the same
+    h, w = 24, 32
     crop = (240, 300, h, w)
+    t0 = time.perf_counter()
+    o.run(frames[:6], crop=crop, nthreads=cores)
+    t_frame = (time.perf_counter() - t0) / 6
+    T = 1
+    for cand in (6, 4, 3, 2):
+        if t_frame * cand * (args.steps + args.warmup) <= 90.0:
+            T = cand
+            break
 
     def step():
         o.run(frames[:T], crop=crop, nthreads=cores)
