@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
         if (kx == 0) rt0[t] = tv.x;
         else if (!RS) rsa[t] += sqrt_approx(fmaf(tv.x, tv.x, tv.y * tv.y));
       };
-#pragma unroll 2
+#pragma unroll
       for (int kx = 0; kx <= K; ++kx) {
         const float2 z = q0[kx];
         float2 ac0 = make_float2(z.x, 0.f), db0 = make_float2(z.y, 0.f);
