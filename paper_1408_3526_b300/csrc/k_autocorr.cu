@@ -216,39 +216,24 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
           v11 = __ffma2_rn(c1[kx - 1], make_float2(t.z, t.w), v11);
         }
         const float4 t0 = *reinterpret_cast<const float4*>(tbuf + gy);
-        if (RS) {
-          take(t0.x, v00, gy, l0, b0, g0);
-          take(t0.z, v01, gy + 1, l0, b0, g0);
-          if (act1) {
-            take(t0.x, v10, gy, l1, b1, g1);
-            take(t0.z, v11, gy + 1, l1, b1, g1);
-          }
-        } else {
-          // the pair's maximum; its row is found again at the end
-          const float m0 = fmaxf(mval(t0.x, v00), mval(t0.z, v01));
-          if (m0 > b0) { b0 = m0; g0 = gy; }
-          if (act1) {
-            const float m1 = fmaxf(mval(t0.x, v10), mval(t0.z, v11));
-            if (m1 > b1) { b1 = m1; g1 = gy; }
-          }
+        take(t0.x, v00, gy, l0, b0, g0);
+        take(t0.z, v01, gy + 1, l0, b0, g0);
+        if (act1) {
+          take(t0.x, v10, gy, l1, b1, g1);
+          take(t0.z, v11, gy + 1, l1, b1, g1);
         }
       }
       // resolve -lx / +lx within each value's best row (-lx has the lower index)
-      auto resolve = [&](const float2 (&cs)[K], float bb, int bg, int l) {
-        // without the dump the kept row pair's first row attaining the maximum
-        // (a row past the pair can only be a later, tie-losing one)
-        if (!RS && bg + 1 < L && !(mval(tbuf[bg].x, row_v(cs, bg)) == bb) &&
-            mval(tbuf[bg + 1].x, row_v(cs, bg + 1)) == bb)
-          ++bg;
+      auto resolve = [&](const float2 (&cs)[K], int bg, int l) {
         const float2 v = row_v(cs, bg);
         const float r0 = tbuf[bg].x;
         const float rp = fmaf(2.f, v.x - v.y, r0), rm = fmaf(2.f, v.x + v.y, r0);
         return bg * L + (rm >= rp ? gc - l : gc + l);
       };
       best = b0;
-      bidx = resolve(c0, b0, g0, l0);
+      bidx = resolve(c0, g0, l0);
       if (act1) {
-        const int i1 = resolve(c1, b1, g1, l1);
+        const int i1 = resolve(c1, g1, l1);
         if (b1 > best || (b1 == best && i1 < bidx)) { best = b1; bidx = i1; }
       }
     }
