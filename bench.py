@@ -85,6 +85,22 @@ def measured_traffic(kernel):
     return int(m1.group(1))
 
 
+def measured_limiter(kernel):
+    """Issue and DRAM utilisation of the kernel from its ncu summary (same
+    validity rule as the traffic), or None."""
+    if measured_traffic(kernel) is None:
+        return None
+    md, _ = PROFILE_OF[kernel]
+    with open(os.path.join(ROOT, md)) as f:
+        text = f.read()
+    m1 = re.search(r"^\| smsp__issue_active \(% of active\) \| ([0-9.]+) \|", text, re.M)
+    m2 = re.search(r"^\| gpu__dram_throughput \(% of peak\) \| ([0-9.]+) \|", text, re.M)
+    if not (m1 and m2):
+        return None
+    return {"issue_active_pct": float(m1.group(1)), "dram_throughput_pct": float(m2.group(1)),
+            "source": md}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -372,7 +388,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames_resident": NFRAMES_RESIDENT,
-                       "l2": "inputs larger than L2 (smoothed state 295 MB per stream)",
+                       "l2": "inputs larger than L2 (smoothed state 299 MB per buffer, two "
+                             "buffers with the frame pipeline)",
                        "parallelism": f"{world} independent streams" if world > 1 else "1 stream",
                        "bytes_per_px_algorithmic": BYTES_PER_PX,
                        "frame_pipeline": pipeline,
@@ -380,6 +397,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved_dom, 1),
                          "peak": hbm, "unit": "GB/s", "frac": round(achieved_dom / hbm, 4),
                          "traffic": measured_traffic(names[dom]), "peak_source": src,
+                         "limiter": measured_limiter(names[dom]),
                          "bytes_per_launch_algorithmic": KERNEL_BYTES_PER_PX[names[dom]] * H * W,
                          "path_achieved": round(achieved_path, 1),
                          "path_frac": round(achieved_path / hbm, 4),
