@@ -275,7 +275,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--profile-steps", type=int, default=20,
                     help="frames of the serial pass that times each kernel alone (roofline)")
     ap.add_argument("--no-pipeline", action="store_true",
