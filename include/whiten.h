@@ -88,6 +88,8 @@ typedef struct {
                            runs on an internal CUDA stream while the search and PEF of frame
                            t run on a second one (the smoothed state is double-buffered,
                            +kpad*4 bytes per pixel); results are identical to pipeline = 0.
+                           With the learned estimator's features on, the spectrum of frame
+                           t+1 also waits for the search of frame t (one feature buffer).
                            The work no longer runs on the caller's CUDA stream: the wh_read_*
                            calls and wh_detect order themselves after it, and raw pointers
                            from wh_output_pointers are valid after wh_stream_sync.
