@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="duration of the oracle's CPU-baseline sample")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--profile-steps", type=int, default=20,
                     help="frames of the serial pass that times each kernel alone (roofline)")
@@ -415,7 +417,7 @@ def main():
             line["config"]["engine"] = "tensor-core shortlist + exact re-rank"
             line["config"]["full_grid_fallback_pixel_frames"] = int(fb.value)
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(frames_h)
+            line["cpu_baseline"] = cpu_baseline(frames_h, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
