@@ -317,10 +317,20 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   const bool dthr = tid < NTW;
 
   // ---- this CTA's share of the (strip, row) units -------------------------------
+  // Units (strip, output row) in strip-major order; every segment a CTA walks
+  // costs its rows plus 2K warm-up rows.  The split is uniform in a cost
+  // coordinate that charges 2K rows at each strip start (cost c -> unit
+  // s*H + max(0, o - 2K), s = c / (H + 2K), o = c mod (H + 2K)), so CTAs
+  // whose range crosses a strip boundary get fewer output rows.
   const int nstrip = (W + TW - 1) / TW;
-  const long long total = (long long)nstrip * H;
-  const long long u0 = total * blockIdx.x / gridDim.x;
-  const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
+  const long long cstrip = (long long)H + 2 * K;
+  const long long ctot = (long long)nstrip * cstrip;
+  auto unit_of = [&](long long c) -> long long {
+    const long long sidx = c / cstrip, o = c - sidx * cstrip;
+    return sidx * H + (o > 2 * K ? o - 2 * K : 0);
+  };
+  const long long u0 = unit_of(ctot * blockIdx.x / gridDim.x);
+  const long long u1 = unit_of(ctot * (blockIdx.x + 1) / gridDim.x);
   __syncthreads();
 
   // Smoothed state of output rows: ring of 3 row segments in shared memory,
