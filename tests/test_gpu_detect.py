@@ -33,3 +33,24 @@ def test_detector_matches_host_threshold():
         # count only
         _, n3, _, _ = s.detect(k_sigma=4.0, max_det=0)
         assert n3 == n
+
+
+def test_detector_after_pipelined_async_pushes():
+    """wh_detect after asynchronous pushes on a pipelined stream sees the last
+    frame's whitened output and velocities (the same as the serial stream's)."""
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    sc = scenes.config1_scene(T=16, H=64, W=80, seed=2)
+    fr = sc.frames.astype(np.float32)
+    with WhitenStream(64, 80, 9, 4, 2.0, 0.25) as s:
+        for t in range(fr.shape[0]):
+            s.push(np.ascontiguousarray(fr[t]))
+        ref = s.detect(k_sigma=3.0, max_det=4096)
+    pin = [torch.from_numpy(fr[t].copy()).pin_memory() for t in range(fr.shape[0])]
+    with WhitenStream(64, 80, 9, 4, 2.0, 0.25, pipeline=True) as s:
+        for t in range(fr.shape[0]):
+            s.push_async(pin[t])
+        got = s.detect(k_sigma=3.0, max_det=4096)
+    assert got[1] == ref[1] and got[2] == ref[2] and got[3] == ref[3]
+    assert np.array_equal(got[0], ref[0])
