@@ -481,12 +481,17 @@ extern "C" {
 int wh_reset_stream(wh_stream* s) {
   if (!s) return WH_EINVAL;
   const size_t npix = size_t(s->H) * s->W;
+  if (s->as) {                // asynchronous copies may still read the buffers reset below
+    if (s->as->in) WH_CU(cudaStreamSynchronize(s->as->in));
+    if (s->as->out) WH_CU(cudaStreamSynchronize(s->as->out));
+  }
   if (s->pipeline) {
     WH_CU(cudaStreamSynchronize(s->st_s));
     WH_CU(cudaStreamSynchronize(s->st_p));
     WH_CU(cudaMemsetAsync(s->Astate_alt, 0, sizeof(float) * npix * s->kpad, s->st));
     s->pef_used[0] = s->pef_used[1] = 0;
     s->pipe_work = 0;
+    s->user_sync = 1;         // the next push orders the internal streams after these memsets
   }
   WH_CU(cudaMemsetAsync(s->obs[0], 0, sizeof(float) * npix * s->Mz, s->st));
   WH_CU(cudaMemsetAsync(s->obs[1], 0, sizeof(float) * npix * s->Mz, s->st));
@@ -512,6 +517,13 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
   const cudaStream_t ss = s->pipeline ? s->st_s : s->st;
   const cudaStream_t sp = s->pipeline ? s->st_p : s->st;
   const int k = int(s->t & 1);
+  if (s->pipeline && s->user_sync) {
+    // the state was reset on the caller's stream: the internal streams start after it
+    WH_CU(cudaEventRecord(s->ev_user, user));
+    WH_CU(cudaStreamWaitEvent(ss, s->ev_user, 0));
+    WH_CU(cudaStreamWaitEvent(sp, s->ev_user, 0));
+    s->user_sync = 0;
+  }
   if (s->pipeline && s->pef_used[k]) WH_CU(cudaStreamWaitEvent(ss, s->ev_pef[k], 0));
   // one feature buffer: with features on, the spectrum of this frame waits
   // until the previous frame's learned search has read it (no overlap there)

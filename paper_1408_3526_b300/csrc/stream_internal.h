@@ -74,6 +74,7 @@ struct wh_stream {
   cudaEvent_t ev_feat;       // the search of the last frame has read the feature buffer
   int pef_used[2];
   int pipe_work;              // kernels were enqueued since the last join
+  int user_sync;              // the state was (re)initialised on the caller's stream
   float* Astate_alt;
   // threshold detector scratch (wh_detect)
   void* d_det;

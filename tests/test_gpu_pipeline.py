@@ -115,3 +115,29 @@ def test_pipeline_learned_mode_identical_to_serial(conf):
     net.close()
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_pipeline_reset_orders_after_the_callers_stream():
+    """wh_reset_stream clears the state on the caller's CUDA stream; with the
+    pipeline the next push (a host frame, which needs nothing else from that
+    stream) must still start after it.  The caller's stream is kept busy across
+    the reset, then the results must equal a fresh stream's."""
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    fr = scenes.config1_scene(T=12, H=H, W=W, seed=12).frames.astype(np.float32)
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP) as s:
+        for t in range(4, 12):
+            s.push(np.ascontiguousarray(fr[t]))
+        ref = (s.read_velocity()[2], s.read_whitened()[0])
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, pipeline=True) as s:
+        for t in range(4):
+            s.push(np.ascontiguousarray(fr[t]))
+        s.sync()
+        torch.cuda._sleep(100_000_000)           # ~50 ms of work queued on the caller's stream
+        s.reset()
+        for t in range(4, 12):
+            s.push(np.ascontiguousarray(fr[t]))
+        got = (s.read_velocity()[2], s.read_whitened()[0])
+    assert np.array_equal(got[0], ref[0])
+    assert np.array_equal(got[1], ref[1])
