@@ -141,3 +141,38 @@ def test_pipeline_reset_orders_after_the_callers_stream():
         got = (s.read_velocity()[2], s.read_whitened()[0])
     assert np.array_equal(got[0], ref[0])
     assert np.array_equal(got[1], ref[1])
+
+
+@pytest.mark.parametrize("pipeline", [False, True])
+def test_learned_mode_async_push_equals_sync(pipeline):
+    """Learned mode through the asynchronous host push (copies overlapped with
+    the kernels) gives the synchronous push's velocities and whitened frames."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1408_3526_b300 import learned
+    from paper_1408_3526_b300.stream import WhitenStream
+    net = learned.MLP(M * M * MZ, 256, 128, 3, seed=4)
+    fr = scenes.config1_scene(T=T, H=H, W=W, seed=13).frames.astype(np.float32)
+    ref = []
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP) as s:
+        assert s.lib.wh_stream_set_learned(s._s, net._m, 0.5) == 0
+        for t in range(T):
+            s.push(np.ascontiguousarray(fr[t]))
+            vx, vy, _, _ = s.read_velocity()
+            w = s.read_whitened()[0] if t >= DELAY else np.zeros((H, W), np.float32)
+            ref.append((vx.copy(), vy.copy(), w.copy()))
+    pin = [torch.from_numpy(fr[t].copy()).pin_memory() for t in range(T)]
+    outs = [[torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(T)]
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, pipeline=pipeline) as s:
+        assert s.lib.wh_stream_set_learned(s._s, net._m, 0.5) == 0
+        for t in range(T):
+            s.push_async(pin[t], *outs[t])
+        s.sync()
+    net.close()
+    for t in range(T):
+        w, x, y = (o.numpy() for o in outs[t])
+        assert np.array_equal(x, ref[t][0]) and np.array_equal(y, ref[t][1]), t
+        if t >= DELAY:
+            assert np.array_equal(w, ref[t][2]), t
