@@ -11,13 +11,15 @@ H, W, M, MZ, VMAX, VSTEP, T = 64, 80, 9, 4, 2.0, 0.25, 14
 DELAY = (MZ - 1) // 2
 
 
-def test_async_push_matches_sync():
+@pytest.mark.parametrize("pipeline,precision", [(False, 0), (True, 0), (True, 16)],
+                         ids=["serial", "pipelined", "pipelined_tc_engine"])
+def test_async_push_matches_sync(pipeline, precision):
     import torch
 
     from paper_1408_3526_b300.stream import WhitenStream
     fr = scenes.config1_scene(T=T, H=H, W=W, seed=5).frames.astype(np.float32)
     ref_w, ref_x, ref_y = [], [], []
-    with WhitenStream(H, W, M, MZ, VMAX, VSTEP) as s:
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, precision=precision) as s:
         for t in range(T):
             s.push(np.ascontiguousarray(fr[t]))
             vx, vy, _, _ = s.read_velocity()
@@ -26,7 +28,7 @@ def test_async_push_matches_sync():
             ref_w.append(s.read_whitened()[0].copy() if t >= DELAY else np.zeros((H, W), np.float32))
     pin = [torch.from_numpy(fr[t].copy()).pin_memory() for t in range(T)]
     outs = [[torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(3)] for _ in range(T)]
-    with WhitenStream(H, W, M, MZ, VMAX, VSTEP) as s:
+    with WhitenStream(H, W, M, MZ, VMAX, VSTEP, precision=precision, pipeline=pipeline) as s:
         idx = []
         for t in range(T):
             idx.append(s.push_async(pin[t], *outs[t]))
