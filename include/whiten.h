@@ -237,7 +237,9 @@ int wh_stream_selftest_status(wh_stream *s, int code);
  * 10.2 MB, held by every GPU that loads the library until the process exits)
  * instead of memory allocated per call or per stream.  Nothing is allocated.
  *   Limits: window <= 15 and grid length L <= 25 (WH_EUNSUP otherwise, with a
- *   message in wh_last_error); frames of any size (processed in chunks).
+ *   message in wh_last_error); frames of any size (processed in chunks); not
+ *   with the frame pipeline (WH_EUNSUP).  A stream in learned mode still gets
+ *   the exact search here (the network is not run).
  *   Sharing: all calls on a device share the array and leave their contents
  *   in it; calls that overlap on the GPU (different CUDA streams or host
  *   threads) race, so serialise them.  Each call clears what must start at 0.
