@@ -53,7 +53,8 @@ def _lowest_argmax(R):
 
 
 @pytest.mark.parametrize("kind", ["flow", "paper_sim", "noise", "constant", "impulse", "nan"])
-@pytest.mark.parametrize("M,Mz,vmax,step", [(15, 6, 3.0, 0.25), (9, 4, 2.0, 0.25), (7, 5, 3.75, 0.25)])
+@pytest.mark.parametrize("M,Mz,vmax,step", [(15, 6, 3.0, 0.25), (9, 4, 2.0, 0.25), (7, 5, 3.75, 0.25),
+                                             (15, 6, 3.75, 0.25)])
 def test_pruned_search_equals_full_evaluation(kind, M, Mz, vmax, step):
     T, H, W = 10, 24, 40
     frames = _frames(kind, T, H, W)
