@@ -108,7 +108,11 @@ int wh_default_params(int window, int temporal_order, wh_params *p);
  *   frame_h, frame_w   frame size (>= 1 each, frame_h * frame_w <= 2^30)
  *   window             spatial window M = 2K+1 (odd, 3..15)
  *   temporal_order     Mz, temporal bins / observer states (2..8)
- *   velocity_grid      search grid for the autocorrelation peak
+ *   velocity_grid      search grid for the autocorrelation peak (at most 31 points
+ *                      per axis).  R(l) is periodic in l with period M, so a grid
+ *                      with 2*vmax >= M holds exact duplicates of its maximum
+ *                      (velocities equal modulo M), decided by rounding; keep
+ *                      vmax <= (M-1)/2 for an unambiguous velocity.
  *   opt                NULL or optional parameters
  *   cuda_stream        a cudaStream_t (NULL = default stream); not owned
  *   out                receives the stream handle
