@@ -176,3 +176,30 @@ def test_learned_mode_async_push_equals_sync(pipeline):
         assert np.array_equal(x, ref[t][0]) and np.array_equal(y, ref[t][1]), t
         if t >= DELAY:
             assert np.array_equal(w, ref[t][2]), t
+
+
+def _random_shapes():
+    from tests.test_gpu_parity_random import _cases
+    return [c[:7] for c in _cases()][:6]
+
+
+@pytest.mark.parametrize("i,Mw,Mzw,vmax,step,Hh,Ww", _random_shapes())
+def test_pipeline_identical_to_serial_random_shapes(i, Mw, Mzw, vmax, step, Hh, Ww):
+    """Frames pushed back to back (no reads in between, so consecutive frames
+    overlap on the device) on seeded random shapes: the pipelined stream's last
+    outputs equal the serial stream's bit for bit."""
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    fr = scenes.small_scene(T=10, H=Hh, W=Ww, seed=300 + i, tex_size=128).frames.astype(np.float32)
+    dev = torch.from_numpy(fr).cuda()
+    res = []
+    for pipeline in (False, True):
+        with WhitenStream(Hh, Ww, Mw, Mzw, vmax, step, pipeline=pipeline) as s:
+            for t in range(fr.shape[0]):
+                s.push(dev[t])
+            vx, vy, vi, _ = s.read_velocity()
+            w, _ = s.read_whitened()
+            res.append((vx, vy, vi, w))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
