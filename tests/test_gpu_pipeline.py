@@ -203,3 +203,23 @@ def test_pipeline_identical_to_serial_random_shapes(i, Mw, Mzw, vmax, step, Hh, 
             res.append((vx, vy, vi, w))
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_pipeline_identical_to_serial_full_size():
+    """The benchmark's configuration (512 x 640, 15 x 15, order 6, grid +-3/0.25),
+    frames pushed back to back: pipelined and serial streams agree bit for bit."""
+    import torch
+
+    from paper_1408_3526_b300.stream import WhitenStream
+    fr = scenes.config2_scene(T=10, H=512, W=640, seed=2).frames.astype(np.float32)
+    dev = torch.from_numpy(fr).cuda()
+    res = []
+    for pipeline in (False, True):
+        with WhitenStream(512, 640, 15, 6, 3.0, 0.25, pipeline=pipeline) as s:
+            for t in range(fr.shape[0]):
+                s.push(dev[t])
+            vx, vy, vi, _ = s.read_velocity()
+            w, _ = s.read_whitened()
+            res.append((vx, vy, vi, w))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
