@@ -168,6 +168,7 @@ inline cudaError_t resident_shape(F* kernel, int threads, size_t smem, ResidentS
 cudaError_t launch_spectrum(const SpecArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr(const AutocorrArgs& a, cudaStream_t st);
 cudaError_t launch_pef(const PefArgs& a, cudaStream_t st);
+cudaError_t pef_init_constants();          // once per device (also done by the first launch)
 cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
 bool spectrum_supported(int M, int Mz);
 cudaError_t spectrum_init_constants();

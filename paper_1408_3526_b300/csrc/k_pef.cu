@@ -17,12 +17,21 @@
 //
 // One CTA per 16 x 16 output tile: the (16+2K)^2 x Mz history tile is rebuilt
 // in shared memory, then every thread filters one pixel with its own velocity.
+#include <atomic>
+#include <cmath>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace wh {
 namespace {
 
 constexpr int kT = 16;
+
+// cos / sin(2pi ((j m) mod Mz) / Mz) per temporal order (index Mz - 3), j = 0..Mz/2,
+// m = 0..Mz-1: the inverse temporal DFT that recovers the last Mz samples from
+// the observer state, read as constant-bank operands
+__constant__ float c_pcs[kMaxMz - 2][kMaxPlanes][kMaxMz], c_psn[kMaxMz - 2][kMaxPlanes][kMaxMz];
 
 template <int M>
 struct PefGeo {
@@ -47,17 +56,8 @@ __global__ void __launch_bounds__(kT * kT / 2) pef_kernel(const PefArgs a) {
   const int x0 = blockIdx.x * kT, y0 = blockIdx.y * kT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* hp = reinterpret_cast<float2*>(smem_raw);        // [MZ][RT][RT]
-  float* cs = reinterpret_cast<float*>(hp + MZ * RT * RT);  // [J+1][MZ] cos, then sin
-  float* sn = cs + (J + 1) * MZ;
   const int tid = threadIdx.y * (kT / 2) + threadIdx.x, nthr = kT * kT / 2;
-  for (int i = tid; i < (J + 1) * MZ; i += nthr) {
-    const int j = i / MZ, m = i % MZ;
-    float s, c;
-    sincospif(2.0f * float((j * m) % MZ) / float(MZ), &s, &c);
-    cs[i] = c;
-    sn[i] = s;
-  }
-  __syncthreads();
+  constexpr int ZI = MZ - 3;
   const size_t plane = size_t(H) * W;
   for (int i = tid; i < RT * RT; i += nthr) {
     const int yy = i / RT, xx = i % RT;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kT * kT / 2) pef_kernel(const PefArgs a) {
       float v = st[0];
 #pragma unroll
       for (int j = 1; j <= J; ++j)
-        v += 2.f * (st[2 * j - 1] * cs[j * MZ + m] + st[2 * j] * sn[j * MZ + m]);
+        v += 2.f * (st[2 * j - 1] * c_pcs[ZI][j][m] + st[2 * j] * c_psn[ZI][j][m]);
       if (EVEN) v += (m & 1) ? -st[MZ - 1] : st[MZ - 1];
       float2* row = hp + (m * RT + yy) * RT + xx;
       row->x = v;
@@ -182,10 +182,37 @@ __global__ void raw_spectrum_kernel(const RawSpecArgs a) {
 
 }  // namespace
 
+// Upload the inverse-DFT tables (all temporal orders) once per device.
+cudaError_t pef_init_constants() {
+  static std::atomic<bool> done[64];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev].load()) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev].load()) return cudaSuccess;
+  static float cs[kMaxMz - 2][kMaxPlanes][kMaxMz], sn[kMaxMz - 2][kMaxPlanes][kMaxMz];
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int z = 3; z <= kMaxMz; ++z)
+    for (int j = 0; j < kMaxPlanes; ++j)
+      for (int m = 0; m < kMaxMz; ++m) {
+        const double ang = two_pi * double((j * m) % z) / double(z);
+        cs[z - 3][j][m] = float(std::cos(ang));
+        sn[z - 3][j][m] = float(std::sin(ang));
+      }
+  e = cudaMemcpyToSymbol(c_pcs, cs, sizeof(cs));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_psn, sn, sizeof(sn));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(true);
+  return e;
+}
+
 template <int M, int MZ>
 static cudaError_t launch_pef_t(const PefArgs& a, cudaStream_t st) {
-  constexpr int RT = PefGeo<M>::RT, J = (MZ - 1) / 2;
-  const size_t smem = sizeof(float2) * size_t(MZ) * RT * RT + sizeof(float) * 2 * size_t(J + 1) * MZ;
+  constexpr int RT = PefGeo<M>::RT;
+  cudaError_t ce = pef_init_constants();
+  if (ce != cudaSuccess) return ce;
+  const size_t smem = sizeof(float2) * size_t(MZ) * RT * RT;
   ResidentShape rs{};
   cudaError_t e = resident_shape(pef_kernel<M, MZ>, kT * kT / 2, smem, &rs);   // sets the smem attribute once
   if (e != cudaSuccess) return e;

@@ -338,6 +338,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
     return rc;
   }
   e = spectrum_init_constants();
+  if (e == cudaSuccess) e = pef_init_constants();
   if (e != cudaSuccess) {
     int rc = set_cuda_err(e, "cudaMemcpyToSymbol");
     free_stream(s);
