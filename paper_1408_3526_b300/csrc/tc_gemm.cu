@@ -405,6 +405,132 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// 256 x 256 output tile per CTA for wide, tall products (EPI_F32 / EPI_BF16):
+// two 128-row sub-tiles share each K block of B, so the B block (the weights
+// of a network layer) is read from L2 once per 256 rows instead of once per
+// 128; the two accumulators take all 512 TMEM columns.  Three stages of
+// (2 x 16 KB of A + 32 KB of B); same warp roles, bounded waits and error flag
+// as tc_gemm_kernel.
+constexpr int kS2 = 3;
+
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const GemmArgs g) {
+  constexpr int BN = 256;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base_u32 = tc::smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+  uint8_t* sA = smem;                                     // kS2 x 2 x 16 KB
+  uint8_t* sB = smem + kS2 * 2 * kBM * kBK * 2;           // kS2 x 32 KB
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kS2 * BN * kBK * 2);
+  uint64_t* empty = full + kS2;
+  uint64_t* accum = empty + kS2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 2 * kBM, n0 = blockIdx.y * BN;
+  const int nk = (g.K + kBK - 1) / kBK;
+  constexpr uint32_t kStageBytes = (2 * kBM + BN) * kBK * 2;
+  constexpr uint32_t kATile = kBM * kBK * 2;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < kS2; ++s) {
+        tc::mbar_init(&full[s], 1);
+        tc::mbar_init(&empty[s], 1);
+      }
+      tc::mbar_init(accum, 1);
+      *abort_flag = 0;
+      tc::fence_mbar_init();
+      tc::tma_prefetch_desc(&tmA);
+      tc::tma_prefetch_desc(&tmB);
+    }
+    __syncwarp();
+    tc::tmem_alloc(tmem_slot, 2 * BN);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kS2;
+      const uint32_t use = kb / kS2;
+      if (kb >= kS2 && !tc::mbar_wait(&empty[s], (use & 1) ^ 1, kWaitNs)) {
+        atomicExch(g.err, 31);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      tc::mbar_expect_tx(&full[s], kStageBytes);
+      tc::tma_load_2d(sA + (2 * s) * kATile, &tmA, &full[s], kb * kBK, m0);
+      tc::tma_load_2d(sA + (2 * s + 1) * kATile, &tmA, &full[s], kb * kBK, m0 + kBM);
+      tc::tma_load_2d(sB + s * BN * kBK * 2, &tmB, &full[s], kb * kBK, n0);
+      issued = kb + 1;
+    }
+    if (*abort_flag)   // let the copies still in flight land before the CTA exits (bounded)
+      for (int i = issued > kS2 ? issued - kS2 : 0; i < issued; ++i)
+        tc::mbar_wait(&full[i % kS2], (i / kS2) & 1, kWaitNs);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = tc::idesc_f16(kBM, BN, g.bf16 != 0);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kS2;
+      const uint32_t use = kb / kS2;
+      if (!tc::mbar_wait(&full[s], use & 1, kWaitNs)) {
+        atomicExch(g.err, 32);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + (2 * s) * kATile);
+      const uint32_t a1 = tc::smem_u32(sA + (2 * s + 1) * kATile);
+      const uint32_t b0 = tc::smem_u32(sB + s * BN * kBK * 2);
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k) {
+        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+        tc::mma_f16(tmem, tc::sdesc_sw128(a0 + 32 * k), tc::sdesc_sw128(b0 + 32 * k), idesc, acc);
+        tc::mma_f16(tmem + uint32_t(BN), tc::sdesc_sw128(a1 + 32 * k), tc::sdesc_sw128(b0 + 32 * k), idesc, acc);
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    if (ok) tc::mma_commit(accum);
+    else tc::mbar_arrive(accum);          // release the epilogue (it checks the flag)
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;                   // TMEM lane quadrant of this warp
+    const bool waited = tc::mbar_wait(accum, 0, 4 * kWaitNs);
+    if (!waited) atomicExch(g.err, 33);
+    tc::tc_fence_after();
+    if (waited && *abort_flag == 0) {
+#pragma unroll 1
+      for (int sub = 0; sub < 2; ++sub) {
+        const int row = m0 + sub * kBM + q * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t r[32];
+          tc::tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(sub * BN + c * 32), r);
+          tc::tmem_ld_wait();
+          epilogue_chunk<BN>(g, r, row, n0 + c * 32, g.bias);
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
 // ---- host side: tensor maps through the driver entry point -----------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -448,6 +574,16 @@ cudaError_t launch_bn(const GemmArgs& g, const void* A, int lda, const void* B, 
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (BN == 256 && g.epi != EPI_TOPK && (long long)g.M >= 2LL * kBM * nsm) {
+    // tall and wide: 256 x 256 tiles, the B block read once per 256 rows
+    const size_t smem2 = 1024 + size_t(kS2) * (2 * kBM + 256) * kBK * 2 + (2 * kS2 + 1) * 8 + 16;
+    ResidentShape rs{};
+    cudaError_t e = resident_shape(tc_gemm2_kernel, 192, smem2, &rs);
+    if (e != cudaSuccess) return e;
+    dim3 grid2((g.M + 2 * kBM - 1) / (2 * kBM), (g.N + 255) / 256);
+    tc_gemm2_kernel<<<grid2, 192, smem2, st>>>(ma, mb, g);
+    return cudaGetLastError();
+  }
   if (g.epi != EPI_TOPK && BN <= 128 && ntiles >= 4LL * nsm) {
     // many tiles: one persistent CTA per SM with a double-buffered accumulator
     // (at BN = 256 the per-tile kernel measured faster: the loads, not the

@@ -29,7 +29,9 @@ def _gemm(A, B, out_bf16=False, bias=None, gelu=False):
                                         (1000, 256, 64, True), (128, 3, 128, False),
                                         # many output tiles: the persistent, double-buffered kernel
                                         (76837, 128, 1350, True), (80000, 100, 232, False),
-                                        (80000, 40, 256, True)])
+                                        (80000, 40, 256, True),
+                                        # tall and wide: 256 x 256 tiles (two 128-row sub-tiles)
+                                        (40000, 256, 1350, True), (45001, 200, 232, False)])
 def test_tc_gemm_matches_torch(M, N, K, bf16):
     import torch
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
@@ -61,6 +63,20 @@ def test_tc_gemm_persistent_bias_gelu_preact():
     import torch
     g = torch.Generator(device="cuda").manual_seed(11)
     M, N, K = 150 * 128 * 4 + 77, 120, 256
+    A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16) * 0.05
+    B = torch.randn((N, K), generator=g, device="cuda").to(torch.bfloat16) * 0.05
+    bias = torch.randn((N,), generator=g, device="cuda")
+    Cm = _gemm(A, B, out_bf16=True, bias=bias, gelu=True)
+    ref = torch.nn.functional.gelu(A.float() @ B.float().T + bias, approximate="tanh")
+    assert (Cm.float() - ref).abs().max().item() < 2e-2
+
+
+def test_tc_gemm_tall_wide_bias_gelu_bf16_out():
+    """256 x 256 tiles (M above two tile rows per SM), ragged M, bias + GELU,
+    BF16 output: the first layer's shape."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(21)
+    M, N, K = 148 * 256 + 1234, 256, 1352
     A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16) * 0.05
     B = torch.randn((N, K), generator=g, device="cuda").to(torch.bfloat16) * 0.05
     bias = torch.randn((N,), generator=g, device="cuda")
