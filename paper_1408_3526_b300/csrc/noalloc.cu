@@ -7,8 +7,10 @@
 // path as wh_push_frame on an existing stream, but its autocorrelation search
 // always uses the tensor-core shortlist with exact FP32 re-evaluation, and all
 // scratch of that search (the F16 copy of the smoothed state, per-pixel norms,
-// the shortlist, the grid table, the error flag) lives in one file-scope
-// __device__ array instead of memory allocated by the library.
+// the shortlist, the grid table) lives in one file-scope __device__ array
+// instead of memory allocated by the library.  A bounded device wait that gives
+// up reports through the stream's own status word (allocated with the stream),
+// so the next synchronising read returns WH_ETIMEOUT as after wh_push_frame.
 //
 // Limits: window M <= 15, grid length L <= 25 (L^2 <= 640 table rows).  Frames
 // of any size are processed in chunks of kChunk pixels.  The array (about
@@ -18,8 +20,8 @@
 // Sharing: every call, from every stream on a device, uses the same array and
 // leaves the last call's contents there.  Calls that overlap on the GPU (on
 // different CUDA streams, or from several host threads) race on it; callers
-// must serialise them (one CUDA stream, or events).  What must start at zero
-// (the error flag) is cleared by each call.
+// must serialise them (one CUDA stream, or events).  Nothing in the array needs
+// to start at zero: every value a call reads was written earlier in that call.
 //
 // Set-up: the first call on a device looks up the array's device address
 // (cudaGetSymbolAddress) with that device current and caches it; make that
@@ -49,8 +51,6 @@ struct NoAllocScratch {
   float l1[kChunk];
   float cval[kChunk * kTiles * 4];
   int cidx[kChunk * kTiles * 4];
-  int err;
-  int nfb;
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -114,6 +114,13 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
   if (e != cudaSuccess) return wh_cuda_fail(e, "cudaGetSymbolAddress");
   const size_t npix = size_t(s->H) * s->W;
   const float* src = frame;
+  if (s->as) {   // after wh_push_frame_async, an output copy may still read the buffers below
+    for (int b = 0; b < 2; ++b)
+      if (s->as->used[b]) {
+        e = cudaStreamWaitEvent(s->st, s->as->ev_out[b], 0);
+        if (e != cudaSuccess) return wh_cuda_fail(e, "cudaStreamWaitEvent");
+      }
+  }
   if (!is_device) {
     e = cudaMemcpyAsync(s->frame, frame, sizeof(float) * npix, cudaMemcpyHostToDevice, s->st);
     if (e != cudaSuccess) return wh_cuda_fail(e, "cudaMemcpyAsync");
@@ -131,8 +138,6 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
   e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return wh_cuda_fail(e, "spectrum kernel");
   // 2. autocorrelation search with all scratch in the static array
-  if ((e = cudaMemsetAsync(&sc->err, 0, sizeof(int), s->st)) != cudaSuccess)
-    return wh_cuda_fail(e, "cudaMemsetAsync");
   noalloc_table_kernel<<<148, 256, 0, s->st>>>(sc->table, s->M, s->L, float(s->vmax), float(s->vstep));
   if ((e = cudaGetLastError()) != cudaSuccess) return wh_cuda_fail(e, "table kernel");
   long long launches = 2;
@@ -145,11 +150,11 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
     ta.Astate = s->Astate + p0 * s->kpad;
     ta.a16 = sc->a16; ta.l1 = sc->l1; ta.cand_val = sc->cval; ta.cand_idx = sc->cidx;
     ta.vidx = s->vidx + p0; ta.vx = s->vx + p0; ta.vy = s->vy + p0;
-    ta.tab_x = s->d_tabx; ta.n_fallback = &sc->nfb;
+    ta.tab_x = s->d_tabx; ta.n_fallback = nullptr;
     if ((e = launch_autocorr_convert(ta, s->st)) != cudaSuccess) return wh_cuda_fail(e, "convert kernel");
     GemmArgs g{};
     g.M = n; g.N = ta.ntile * 128; g.K = s->M * s->M; g.bf16 = 0; g.epi = EPI_TOPK;
-    g.cand_val = sc->cval; g.cand_idx = sc->cidx; g.n_valid = s->L * s->L; g.err = &sc->err;
+    g.cand_val = sc->cval; g.cand_idx = sc->cidx; g.n_valid = s->L * s->L; g.err = s->d_err;
     if ((e = tc_gemm(g, sc->a16, kKg, sc->table, kKg, 128, s->st)) != cudaSuccess)
       return wh_cuda_fail(e, "tensor-core autocorrelation");
     if ((e = launch_autocorr_rerank(ta, s->st)) != cudaSuccess) return wh_cuda_fail(e, "re-rank kernel");

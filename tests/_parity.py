@@ -5,10 +5,16 @@ Tolerances (the method's acceptance bar):
   spectra   per pixel max_k |S_gpu - S_ref| / RMS_k |S_ref|   <= 1e-4
   velocity  grid index identical on >= 99.9% of pixels, within one grid step
             elsewhere, and every mismatch a near tie of the oracle's R'
-  whitened  max |E_gpu - E_ref| <= 1e-3 x input RMS, with E_ref computed by
-            the oracle using the GPU's velocity indices (the whitened value
-            for a given velocity field is unique; the field itself is checked
-            by the velocity criterion)
+  whitened  max |E_gpu - E_ref| <= 1e-3 x input RMS, E_ref the oracle's own
+            whitened output (its own velocity field), over every pixel whose
+            velocity index equals the oracle's (E at a pixel depends on the
+            velocity of that pixel in the same push only); the same error is
+            also held to 1e-3 x the clutter RMS (the input's standard
+            deviation, without the DC offset, ten times smaller than the input
+            RMS in these scenes).  At the near-tie pixels where the indices
+            differ the error is reported, and E is compared with the oracle's
+            filter run on the GPU's velocity field (the whitened value for a
+            given field is unique), at the same bar.
 """
 from __future__ import annotations
 
@@ -17,6 +23,7 @@ import numpy as np
 SPEC_TOL = 1e-4
 VEL_EXACT_FRAC = 0.999
 WHITE_TOL_REL = 1e-3
+WHITE_TOL_CLUTTER = 1e-3
 TIE_TOL = 2e-5          # R' near tie: (max - R'[gpu]) / max|R'| below this
 
 
@@ -100,3 +107,27 @@ def whitened_err(gpu_w, ref_w, frames, delay):
     rms = float(np.sqrt(np.mean(frames.astype(np.float64) ** 2)))
     d = np.abs(gpu_w[delay:] - ref_w[delay:])
     return float(np.nanmax(d)) / rms
+
+
+def whitened_report(gpu_w, gpu_vel, ref_w, ref_vel, frames, delay):
+    """Unconditioned whitened error against the oracle's own output.
+
+    gpu_w / ref_w [T][h][w]: E of frame t - delay produced at push t (NaN or
+    unused before t = delay); gpu_vel / ref_vel [T][h][w]: velocity indices of
+    push t, which tune the filter of that push pixel by pixel.  Returns a dict:
+    'matched' max |dE| / input RMS over pixels whose indices agree,
+    'matched_clutter' the same over the clutter RMS (standard deviation of the
+    input), 'mismatched' max |dE| / input RMS over the others (0 if none),
+    'mismatched_frac' their share of the compared pixel-frames."""
+    f64 = frames.astype(np.float64)
+    rms = float(np.sqrt(np.mean(f64 ** 2)))
+    crms = float(np.std(f64))
+    d = np.abs(gpu_w[delay:].astype(np.float64) - ref_w[delay:])
+    same = gpu_vel[delay:] == ref_vel[delay:]
+    dm = d[same]
+    dn = d[~same]
+    return {"matched": float(np.nanmax(dm)) / rms if dm.size else 0.0,
+            "matched_clutter": float(np.nanmax(dm)) / crms if dm.size else 0.0,
+            "mismatched": float(np.nanmax(dn)) / rms if dn.size else 0.0,
+            "mismatched_clutter": float(np.nanmax(dn)) / crms if dn.size else 0.0,
+            "mismatched_frac": float(np.mean(~same)) if same.size else 0.0}

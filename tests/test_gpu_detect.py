@@ -54,3 +54,52 @@ def test_detector_after_pipelined_async_pushes():
         got = s.detect(k_sigma=3.0, max_det=4096)
     assert got[1] == ref[1] and got[2] == ref[2] and got[3] == ref[3]
     assert np.array_equal(got[0], ref[0])
+
+
+def test_detector_matches_oracle_detections():
+    """The detector's pixel set against the same sigma rule applied to the FP64
+    oracle's own whitened frame (Sec. 1: a threshold on the whitened output
+    extracts candidate detections).  Sets must agree except at pixels whose
+    oracle value lies within the whitened tolerance (1e-3 x input RMS, plus the
+    sigma difference times k) of the oracle's threshold; the velocity tag of a
+    common detection equals the oracle's velocity there, or a grid step away at
+    an oracle near-tie."""
+    import oracle
+    from paper_1408_3526_b300.stream import WhitenStream
+    from tests import _parity as P
+    T, H, W, k = 24, 64, 64, 3.0
+    sc = scenes.config1_scene(T=T, H=H, W=W, seed=1)
+    with WhitenStream(H, W, 9, 4, 2.0, 0.25) as s:
+        for t in range(T):
+            s.push(np.ascontiguousarray(sc.frames[t]))
+        det, n, sigma, di = s.detect(k_sigma=k, max_det=H * W)
+        L = s.L
+        vmax, step = s.vmax, s.step
+    o = oracle.Oracle(9, 4, 2.0, 0.25)
+    ref = o.run(sc.frames)
+    assert di == T - 1 - o.mpz
+    e_ref = ref["whitened"][T - 1]
+    sig_ref = float(np.sqrt(np.mean(e_ref ** 2)))
+    rms = float(np.sqrt(np.mean(sc.frames.astype(np.float64) ** 2)))
+    assert abs(sigma - sig_ref) <= P.WHITE_TOL_REL * rms
+    thr = k * sig_ref
+    tol = P.WHITE_TOL_REL * rms + k * abs(sigma - sig_ref)
+    ref_set = set(zip(*np.nonzero(e_ref >= thr)))
+    got_set = set(zip(det["y"].tolist(), det["x"].tolist()))
+    assert len(got_set) == n
+    for (y, x) in ref_set ^ got_set:
+        assert abs(e_ref[y, x] - thr) <= tol, (y, x, e_ref[y, x], thr)
+    vi = ref["vel_index"][T - 1]
+    for d in det:
+        y, x = int(d["y"]), int(d["x"])
+        if (y, x) not in ref_set:
+            continue
+        rx, ry = vi[y, x] % L, vi[y, x] // L
+        gx = int(round((float(d["vx"]) + vmax) / step))
+        gy = int(round((float(d["vy"]) + vmax) / step))
+        assert max(abs(gx - rx), abs(gy - ry)) <= 1
+        if (gx, gy) == (rx, ry):
+            assert abs(float(d["value"]) - e_ref[y, x]) <= P.WHITE_TOL_REL * rms
+    print(f"\n[detect vs oracle] {len(ref_set)} oracle detections, {n} GPU, "
+          f"{len(ref_set ^ got_set)} at the threshold edge", flush=True)
+    assert len(ref_set) > 0

@@ -8,6 +8,7 @@ import pytest
 import oracle
 from oracle import mlp as omlp
 from paper_1408_3526_b300 import scenes
+from tests import _mlp_bounds as B
 
 pytestmark = pytest.mark.gpu
 
@@ -48,10 +49,13 @@ def test_mlp_forward_matches_oracle(n_in, h1, h2):
     x[:, :n_in] = rng.normal(0, 1, (n, n_in))
     xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
     y = net.forward(xb).cpu().numpy()
-    yr, _ = omlp.forward(_bf16_params(p, n_in, h1, h2), xb.float().cpu().numpy()[:, :n_in], n_in, h1, h2)
-    scale = np.abs(yr).max()
-    # BF16 hidden activations (8-bit significand): a few 1e-3 of the output scale
-    assert np.max(np.abs(y - yr)) <= 3e-2 * scale, (np.max(np.abs(y - yr)), scale)
+    yr, e_y, _ = B.forward_bounds(_bf16_params(p, n_in, h1, h2), xb.float().cpu().numpy()[:, :n_in],
+                                  n_in, h1, h2)
+    # element-wise: every output within twice its propagated rounding bound
+    d = np.abs(y[:, :3] - yr)
+    print(f"\n[mlp forward {n_in}-{h1}-{h2}] max |dy| / bound {np.max(d / e_y):.3f}, "
+          f"median bound / |y| {np.median(e_y / np.maximum(np.abs(yr), 1e-30)):.2e}", flush=True)
+    assert np.all(d <= 2 * e_y), np.max(d / e_y)
     net.close()
 
 
@@ -64,17 +68,24 @@ def test_mlp_gradients_match_oracle():
     x = np.zeros((n, ld), np.float32)
     x[:, :n_in] = rng.normal(0, 1, (n, n_in))
     xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
-    t = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    pb = _bf16_params(p, n_in, h1, h2)
+    xr = xb.float().cpu().numpy()[:, :n_in].astype(np.float64)
+    yr, e_y, _ = B.forward_bounds(pb, xr, n_in, h1, h2)
+    t = rng.uniform(-1, 1, (n, 2))
+    for _ in range(40):                 # keep every confidence label away from its flip
+        bad = B.threshold_margin(yr, e_y, t, 0.25) < 8
+        if not bad.any():
+            break
+        t[bad] += 0.03
+    t = t.astype(np.float32)
     net.train_step(xb, torch.from_numpy(t).cuda(), 0.25, lr=0.0, apply=False)
     g = net.grads().astype(np.float64)
-    _, gr, _ = omlp.loss_and_grads(_bf16_params(p, n_in, h1, h2), xb.float().cpu().numpy()[:, :n_in], t.astype(np.float64),
-                                   0.25, n_in, h1, h2)
-    o = 0
-    for name, size in [("W1", h1 * n_in), ("b1", h1), ("W2", h2 * h1), ("b2", h2), ("W3", 3 * h2), ("b3", 3)]:
-        a, b = g[o:o + size], gr[o:o + size]
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert rel < 5e-2, (name, rel)
-        o += size
+    gr, e, _, _ = B.grad_bounds(pb, xr, t.astype(np.float64), 0.25, n_in, h1, h2)
+    # element-wise: every gradient entry within twice its propagated rounding bound
+    for name, sl in B.param_slices(n_in, h1, h2).items():
+        d = np.abs(g[sl] - gr[sl])
+        print(f"\n[mlp grad {name}] max |dg| / bound {np.max(d / e[sl]):.3f}", flush=True)
+        assert np.all(d <= 2 * e[sl]), (name, float(np.max(d / e[sl])))
     net.close()
 
 

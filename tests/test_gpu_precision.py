@@ -6,8 +6,12 @@ temporal order 6, velocity grid +-2 step 1/4.  Reported per output:
   spectrum  per-pixel max |S - S_ref| / RMS |S_ref| (crop run, 40 frames)
   velocity  grid-index agreement and max grid-step distance (sampled pixels,
             every frame, 500 frames: shows whether the error grows)
-  whitened  max |E - E_ref| / input RMS, with E_ref computed for the same
-            velocity field, first and second half of the sequence
+  whitened  max |E - E_ref| / input RMS against the oracle's own whitened
+            output (its own velocity field): at the pixels whose velocity
+            index equals the oracle's, and at all pixels (the latter includes
+            what each mode's velocity misses cost); also with E_ref computed
+            for the mode's velocity field (the filter's numerics alone);
+            first and second half of the sequence, and over the clutter RMS
 """
 import json
 import os
@@ -62,7 +66,11 @@ def test_precision_study_config3():
         steps = 0
         werr = [0.0, 0.0]
         wsq = [[], []]
+        uall = [0.0, 0.0]
+        umatch = [0.0, 0.0]
+        usq = [[], []]
         rms = float(np.sqrt(np.mean(fr.astype(np.float64) ** 2)))
+        crms = float(np.std(fr.astype(np.float64)))
         for (y, x), ref in refs.items():
             gi = vel[:, y, x].astype(np.int32)
             ri = ref["vel_index"][:, 0, 0]
@@ -77,7 +85,21 @@ def test_precision_study_config3():
             werr[1] = max(werr[1], float(np.nanmax(e[half:])) / rms)
             wsq[0].append(e[o.mpz:half] ** 2)
             wsq[1].append(e[half:] ** 2)
+            # against the oracle's own output (unconditioned)
+            u = np.abs(white[:, y, x] - ref["whitened"][:, 0, 0])
+            m = gi == ri
+            for hsel, sl in enumerate((slice(o.mpz, half), slice(half, T))):
+                uall[hsel] = max(uall[hsel], float(np.max(u[sl])) / rms)
+                if m[sl].any():
+                    umatch[hsel] = max(umatch[hsel], float(np.max(u[sl][m[sl]])) / rms)
+                usq[hsel].append(u[sl] ** 2)
         report[name] = {
+            "whitened_vs_oracle_max_over_rms_all_first_half": uall[0],
+            "whitened_vs_oracle_max_over_rms_all_second_half": uall[1],
+            "whitened_vs_oracle_max_over_rms_matched_first_half": umatch[0],
+            "whitened_vs_oracle_max_over_rms_matched_second_half": umatch[1],
+            "whitened_vs_oracle_rms_over_rms_all": float(np.sqrt(np.mean(np.concatenate(usq[0] + usq[1])))) / rms,
+            "whitened_vs_oracle_max_over_clutter_rms_all": max(uall) * rms / crms,
             "velocity_identical_first_half": float(np.mean(np.concatenate(same[0]))),
             "velocity_identical_second_half": float(np.mean(np.concatenate(same[1]))),
             "velocity_max_grid_steps": steps,
@@ -112,6 +134,8 @@ def test_precision_study_config3():
         assert r["velocity_identical_second_half"] >= 0.999
         assert r["velocity_max_grid_steps"] <= 1
         assert r["whitened_max_err_over_rms_second_half"] <= 1e-3
+        assert r["whitened_vs_oracle_max_over_rms_matched_first_half"] <= 1e-3
+        assert r["whitened_vs_oracle_max_over_rms_matched_second_half"] <= 1e-3
     for name in ("tc_fp16", "tc_bf16"):
         assert report[name]["whitened_max_err_over_rms_second_half"] <= 1e-3
     assert report["spectrum_rel_err"] <= 1e-4
