@@ -60,12 +60,29 @@ extern "C" {
  *   error window (whole grid when the shortlist could be incomplete).
  * WH_PREC_TC_FP16 / WH_PREC_TC_BF16: precision study, the tensor-core F16 or
  *   BF16 contraction (F32 accumulation) decides alone.
- * WH_PREC_CUDA_CORES: accepted for clarity, same as the default. */
+ * WH_PREC_TC_SEPARABLE: the exact FP32 argmax by the separable evaluation
+ *   with its first stage (T for every grid row, a [pixels x 32] x [32 x 2L]
+ *   contraction) on tcgen05 tensor cores in TF32: the row upper bounds come
+ *   from the tensor-core T widened by the TF32 error, and only the rows whose
+ *   bound reaches the best row's exact value are evaluated in FP32 on CUDA
+ *   cores, so the velocity is identical to the CUDA-core search's.  Windows
+ *   5..15, grids up to 31 x 31.
+ * WH_PREC_CUDA_CORES: the separable evaluation on CUDA cores only.
+ * WH_PREC_SPEC_F64 (combinable with the search flags): the precision form of the
+ *   recursive spectrum: the spatial sums (x-direction DFT, comb differences and
+ *   y-direction resonator running sums, the box sums of the high-pass, the
+ *   Hann convolution and the power) in double precision with double
+ *   twiddles, the rounding that the comb/resonator pole-zero cancellation on
+ *   the unit circle would otherwise accumulate (Sec. 1); the observer, the
+ *   smoothed state and the search stay FP32.  Several times slower (one CTA
+ *   per SM, the GPU's reduced FP64 rate); no learned-estimator features. */
 #define WH_PREC_FP32          0
 #define WH_PREC_TC_FP16       1
 #define WH_PREC_TC_BF16       2
 #define WH_PREC_CUDA_CORES    8
 #define WH_PREC_TC_SHORTLIST 16
+#define WH_PREC_TC_SEPARABLE 32
+#define WH_PREC_SPEC_F64     64
 
 /* Velocity grid: {-vmax, -vmax + step, ..., +vmax} on both axes
  * (Sec. 3: l_x = l_y = [-8 .. 8]/4, a 17 x 17 grid at vmax = 2, step 1/4).
@@ -124,8 +141,11 @@ int wh_create_stream(int frame_h, int frame_w, int window, int temporal_order,
 
 /*
  * Push one frame (float32 [h][w]); runs the whole per-pixel path for it:
- * observer + spatial SDFT + high-pass + Hann + power + smoothing, the
- * autocorrelation search, and the prediction-error filter.  Asynchronous on
+ * observer + spatial SDFT + high-pass + Hann + power + smoothing (Sec. 1-2,
+ * Eq. (6)-(7) and (9)), the autocorrelation search (Eq. (10) on the lz = 1
+ * slice, smoothed as described after Eq. (10)), and the prediction-error
+ * filter (Eq. (1)-(2), equal to Eq. (4) with the coefficients of Eq. (8)).
+ * Asynchronous on
  * the stream's CUDA stream; a host frame is copied first (the copy is done
  * before the call returns only if the memory is pageable).
  * Errors: WH_EINVAL (NULL), WH_ECUDA.
@@ -246,7 +266,14 @@ int wh_stream_selftest_status(wh_stream *s, int code);
  *   the exact search here (the network is not run).
  *   Sharing: all calls on a device share the array and leave their contents
  *   in it; calls that overlap on the GPU (different CUDA streams or host
- *   threads) race, so serialise them.  Each call clears what must start at 0.
+ *   threads) race, so serialise them.  No part of the array needs to start at
+ *   zero (each call writes everything it reads).
+ *   Errors on the device: a bounded wait that gives up sets the stream's own
+ *   status word, so the next synchronising call (wh_read_*, wh_stream_sync)
+ *   returns WH_ETIMEOUT, as after wh_push_frame.  After wh_push_frame_async on
+ *   the same stream the call first waits (on the device) for its output copies.
+ *   Frames pushed here are not timed by wh_profile_* and not counted by
+ *   wh_stream_learned_stats.
  *   Set-up: the first call on a device looks up the array's device address;
  *   make that first call before any stream capture.
  * Errors: WH_EINVAL, WH_EUNSUP, WH_ECUDA.
@@ -256,14 +283,18 @@ int wh_push_frame_noalloc(wh_stream *s, const float *frame, int is_device);
 /*
  * Whitened (prediction-error) frame E for frame index t - m'_z, where t is
  * the index of the last frame pushed (first frame = 0), written to
- * out[h][w].  *frame_index (may be NULL) receives t - m'_z.
+ * out[h][w]: E = I(n - m') - I^(n - m') with the prediction of Eq. (1)/(4),
+ * delayed by the temporal part m'_z of the filter delay m' (Sec. 2, Eq. (2);
+ * Sec. 3 uses m' = K).  *frame_index (may be NULL) receives t - m'_z.
  * Errors: WH_ENOTREADY before m'_z + 1 frames, WH_EINVAL, WH_ECUDA.
  */
 int wh_read_whitened(wh_stream *s, float *out, int is_device, long long *frame_index);
 
 /*
  * Background velocity estimate of the last frame pushed, in pixels/frame:
- * vx[h][w], vy[h][w] (either may be NULL).  vidx (may be NULL) receives the
+ * vx[h][w], vy[h][w] (either may be NULL): v^ = l^/lz with l^ the grid point
+ * of the largest smoothed autocorrelation on the lz = 1 slice (Sec. 2,
+ * Eq. (10) and the text after it).  vidx (may be NULL) receives the
  * flat grid index iy*L + ix (int32 [h][w]) with vx = -vmax + ix*step.
  * *frame_index receives t.  Errors: WH_ENOTREADY before the first frame.
  */
@@ -295,6 +326,22 @@ int wh_read_spectrum(wh_stream *s, int kind, void *out, int is_device);
  * Errors: WH_ENOTREADY (no frame pushed), WH_EINVAL, WH_ENOMEM, WH_ECUDA.
  */
 int wh_read_autocorr(wh_stream *s, float *out, int is_device);
+
+/*
+ * The constant stage-1 operand of the tensor-core separable search
+ * (WH_PREC_TC_SEPARABLE), for inspection and tests; host only, no GPU needed.
+ * Writes 64 x 32 floats: row n = 2 gy + c holds the coefficients of Re T (c = 0)
+ * or Im T (c = 1) of grid row gy (l = -vmax + gy * step) in T(kx, l) =
+ * sum_ky Q(kx, ky) e^{j2pi ky l/M} (the separable form of Eq. (10)), as
+ * functions of a pixel's Q sums: column 4 (ky - 1) + {0, 1, 2, 3} for
+ * Q(kx, ky) +- Q(kx, -ky) (real sum, real difference, imaginary sum,
+ * imaginary difference), ky = 1..K, column 28 / 29 for Re / Im Q(kx, 0);
+ * values rounded to TF32 and stored in the tensor cores' 128-byte-swizzled
+ * K-major layout (element (n, k) at n * 32 + ((k / 4) ^ (n % 8)) * 4 + k % 4).
+ *   window      M (odd, 5..15); grid_len L (odd, <= 31); step the grid step
+ * Returns 0, or -1 (WH_EINVAL) for arguments out of range.
+ */
+int wh_tcsep_operand(int window, int grid_len, double step, float *out);
 
 /* Grid length L and the output delay m'_z of a stream. */
 int wh_stream_info(const wh_stream *s, int *grid_len, int *delay_z, int *band,
@@ -382,9 +429,16 @@ int wh_mlp_train_step(wh_mlp *m, const void *x, int ldx, int n, const float *tar
                       float lr, float weight_decay, int apply, float *stats);
 
 /* Per-pixel features for the network: (log2(P(k)/sum_k P(k) + 1e-6) + 10)/10 of the
- * high-passed, Hann-windowed power of all M*M*Mz bins, order [kz][ky][kx] as
- * in wh_read_spectrum, BF16 rows of stride *ld (>= M*M*Mz, padding zero).
- * set_features(1) makes every push write them; read copies the last frame's. */
+ * high-passed, Hann-windowed power, sum over all M*M*Mz bins, order [kz][ky][kx]
+ * as in wh_read_spectrum, BF16 rows of stride *ld (padding zero).
+ * set_features(1): all M*M*Mz bins.  set_features(2): one feature per mirror
+ * pair, since P(-k) = P(k) for a real input (Eq. (9)): the bins k whose flat
+ * index is not larger than that of -k (kz -> -kz mod Mz, ky -> -ky, kx -> -kx),
+ * in increasing order: (M*M*Mz + 2 - Mz % 2) / 2 features (676 at 15 x 15 x 6);
+ * a network on them equals one on all bins whose first-layer columns of k and
+ * -k are summed.  0 turns features off.  Every push then writes them; read
+ * copies the last frame's.  In learned mode the layout follows the network's
+ * input width. */
 int wh_stream_set_features(wh_stream *s, int enable);
 int wh_read_features(wh_stream *s, void *out, int is_device, int *ld);
 /* Learned velocity mode: per frame the network (not owned; must outlive its
@@ -414,12 +468,22 @@ int wh_stream_learned_stats(wh_stream *s, long long *frames, long long *fallback
  *   stream runs on one of n_cuda_streams CUDA streams, so different streams'
  *   frames overlap on the device while one stream's frames stay in order.
  *   wait    blocks until a request completes; returns its whitened frame
- *           (if keep_results) and its latency = completion - arrival.
+ *           (if keep_results) and its latency = completion - arrival.  Each
+ *           request is returned once and then forgotten (a second wait on
+ *           the same id returns WH_EINVAL).  The result is copied off the
+ *           stream's pinned buffer by the dispatcher thread, not inside the
+ *           CUDA host callback.
  *   stats   p50/p99 latency of served frames, served Mpixel/s between the
  *           first arrival and the last completion, served/shed/submitted.
  */
 typedef struct wh_server wh_server;
 long long wh_stream_device_bytes(int h, int w, int window, int temporal_order, wh_vgrid grid);
+/* The same with the stream's optional parameters (NULL = defaults): adds the
+ * frame pipeline's second smoothed-state buffer, the tensor-core shortlist's
+ * scratch, the separable search's operand and the debug dump.  wh_server_open
+ * admits a stream against this figure. */
+long long wh_stream_device_bytes_opt(int h, int w, int window, int temporal_order, wh_vgrid grid,
+                                     const wh_params *opt);
 int wh_server_create(double hbm_budget_bytes, int max_inflight, int queue_limit, int n_cuda_streams,
                      int keep_results, wh_server **out);
 int wh_server_open(wh_server *srv, int h, int w, int window, int temporal_order, wh_vgrid grid,

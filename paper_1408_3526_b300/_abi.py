@@ -27,6 +27,8 @@ WH_PREC_TC_FP16 = 1
 WH_PREC_TC_BF16 = 2
 WH_PREC_CUDA_CORES = 8
 WH_PREC_TC_SHORTLIST = 16
+WH_PREC_TC_SEPARABLE = 32
+WH_PREC_SPEC_F64 = 64
 
 WH_SPEC_RAW = 0
 WH_SPEC_WINDOWED = 1
@@ -76,6 +78,7 @@ _SIGS = {
     "wh_stream_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong)]),
     "wh_stream_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+    "wh_tcsep_operand": (C.c_int, [C.c_int, C.c_int, C.c_double, _VP]),
     "wh_output_pointers": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
                                      C.POINTER(_VP)]),
     "wh_profile_enable": (C.c_int, [_VP, C.c_int]),
@@ -98,6 +101,8 @@ _SIGS = {
     "wh_stream_set_learned": (C.c_int, [_VP, _VP, C.c_float]),
     "wh_stream_learned_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "wh_stream_device_bytes": (C.c_longlong, [C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid]),
+    "wh_stream_device_bytes_opt": (C.c_longlong, [C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid,
+                                                  C.POINTER(wh_params)]),
     "wh_server_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
     "wh_server_open": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, C.c_int, wh_vgrid, C.POINTER(wh_params),
                                  C.POINTER(C.c_int)]),

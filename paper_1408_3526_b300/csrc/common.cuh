@@ -56,13 +56,16 @@ struct SpecArgs {
   float2* dump_win;             // optional [H*W][Mz][M][M]
   float* dump_pow;              // optional [H*W][Mz][M][M]
   // learned-estimator features (optional): per pixel, (log2(P(k)/sum P + 1e-6) + 10)/10 of
-  // all M*M*Mz bins in the order [kz][ky][kx] (kz = -J.., ky, kx = -K..), BF16,
-  // row stride feat_ld; feat_gather[b] = offset (c*M + iy) of bin b (or of its
-  // mirror -b) in a pixel's power block.
+  // the bins in the order [kz][ky][kx] (kz = -J.., ky, kx = -K..) -- all M*M*Mz of them,
+  // or only those whose mirror -b does not come earlier (P(-b) = P(b)) -- BF16, row
+  // stride feat_ld; feat_gather[i] = offset (c*M + iy) of feature i's bin (or of its
+  // mirror) in a pixel's power block.
   void* feat;
   int feat_ld;
+  int feat_n;                   // features per pixel (<= M*M*Mz): all bins, or one per mirror pair
   const int* feat_gather;
   int* err;                     // device status word: set nonzero if a bounded wait gives up
+  int f64;                      // 1: the precision form (spatial sums in double)
 };
 
 struct AutocorrArgs {
@@ -98,6 +101,23 @@ struct AutocorrTcArgs {
   float* vy;
   const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
   int* n_fallback;              // optional counter of pixels evaluated on the whole grid
+};
+
+// Autocorrelation search with the separable stage on tensor cores
+// (k_autocorr_tcsep.cu); bop: the stage-1 operand [64][32] TF32 values in the
+// 128-byte-swizzled K-major layout (row n = 2 gy + re/im, column k = 4 (ky-1) +
+// {sr, dr, si, di}, k = 28/29: Qr/Qi(kx, 0)).
+struct TcSepArgs {
+  int npix, M, L, kpad;
+  float vmax, vstep;
+  float wcoef;                  // bound widening per unit of sum |Q sums| (TF32 error)
+  const float* Astate;
+  int* vidx;
+  float* vx;
+  float* vy;
+  const float* bop;
+  const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
+  int* err;
 };
 
 struct PefArgs {
@@ -173,9 +193,13 @@ cudaError_t launch_raw_spectrum(const RawSpecArgs& a, cudaStream_t st);
 bool spectrum_supported(int M, int Mz);
 cudaError_t spectrum_init_constants();
 int spectrum_threads(int M, int Mz);      // block size of the spectrum kernel
-size_t spectrum_smem(int M, int Mz);      // its dynamic shared memory (bytes)
+size_t spectrum_smem(int M, int Mz, bool f64 = false);   // its dynamic shared memory (bytes)
 bool autocorr_tc_supported(int M);
 cudaError_t launch_autocorr_convert(const AutocorrTcArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr_rerank(const AutocorrTcArgs& a, cudaStream_t st);
+bool autocorr_tcsep_supported(int M, int L);
+cudaError_t launch_autocorr_tcsep(const TcSepArgs& a, cudaStream_t st);
+// Stage-1 operand of the tensor-core separable search (2048 floats, see TcSepArgs)
+void build_tcsep_operand(int M, int L, double vstep, float* out);
 
 }  // namespace wh

@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
     // maximum (nor a tie), so only the row pairs with a row reaching it are
     // evaluated, in increasing order, and the argmax is exactly that of the
     // full evaluation.
-    constexpr float kUbRel = 1.0f / 4096.0f;
+    // An absolute floor of 2^-56 covers |T| whose square underflows (|T| below
+    // 2^-63 per kx) and the absolute rounding of R in the subnormal range.
+    constexpr float kUbRel = 1.0f / 4096.0f, kUbAbs = 1.3877788e-17f;
     const unsigned all_pairs = (1u << ((L + 1) / 2)) - 1u;
     unsigned pairs = all_pairs;
     if (!RS) {
@@ -161,7 +163,8 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
       int ur = 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        u[t] = own[t] ? fmaf(2.f * rsa[t], 1.f + kUbRel, fmaf(kUbRel, fabsf(rt0[t]), rt0[t])) : -INFINITY;
+        u[t] = own[t] ? fmaf(2.f * rsa[t], 1.f + kUbRel, fmaf(kUbRel, fabsf(rt0[t]), rt0[t])) + kUbAbs
+                      : -INFINITY;
         if (u[t] > um || (u[t] == um && own[t] && rows[t] < ur)) { um = u[t]; ur = rows[t]; }
       }
 #pragma unroll

@@ -41,11 +41,16 @@
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
 namespace wh {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
 namespace {
 
@@ -61,6 +66,7 @@ constexpr int kSegRows = 256;       // longest run of the y-recursion (output ro
 constexpr int kMaxK = (kMaxM - 1) / 2;
 __constant__ float2 c_rwx[7][kMaxK], c_rwy[7][kMaxK], c_rnwy[7][kMaxK];
 __constant__ float2 c_rcx[7][kMaxK], c_rcy[7][kMaxK], c_rncy[7][kMaxK];
+__constant__ double2 c_dw[7][kMaxM], c_dc[7][kMaxM];   // the same twiddles in double (index ky + K)
 __constant__ float2 c_lam[kZN][kMaxPlanes];
 __constant__ float2 c_hz[kZN];
 __constant__ float c_cz[kZN][kMaxPlanes];
@@ -97,8 +103,11 @@ __host__ __device__ constexpr int pick_pstride(int tw, int nct, int M, int minps
   return best;
 }
 
-// Compile-time geometry of one (M, Mz) configuration.
-template <int M, int MZ>
+// Compile-time geometry of one (M, Mz) configuration.  F64: the spatial sums
+// (x-DFT, comb differences, y-resonators, box sums, Hann and high-pass
+// correction) in double precision, the precision form; element sizes of
+// their buffers double.
+template <int M, int MZ, bool F64 = false>
 struct SG {
   static constexpr int K = (M - 1) / 2;
   static constexpr int J = (MZ - 1) / 2;                  // complex planes 1..J
@@ -143,15 +152,16 @@ struct SG {
   // first channel of plane p (channel order: plane 0 kx = 0..K, complex planes
   // kx = -K..K, Nyquist plane kx = 0..K)
   __host__ __device__ static constexpr int base(int p) { return p == 0 ? 0 : (K + 1) + (p - 1) * M; }
-  // shared-memory layout (bytes)
-  static constexpr size_t O_TWR = 0;                                           // float2 [NPL][RW]
-  static constexpr size_t O_RING = al16(O_TWR + 8ull * NPL * RW);              // float2 [M+1][NCHY][TW]
-  static constexpr size_t O_DCR = al16(O_RING + 8ull * (M + 1) * NCHY * TW);   // float2 [M+1][NPL][TW]
-  static constexpr size_t O_XW = al16(O_DCR + 8ull * (M + 1) * NPL * TW);      // float2 [K+1][M]
-  static constexpr size_t O_XW4 = al16(O_XW + 8ull * (K + 1) * M);             // float4 [K+1][M]
+  // shared-memory layout (bytes); E2 = bytes of a complex element of the sums
+  static constexpr size_t E2 = F64 ? 16 : 8;
+  static constexpr size_t O_TWR = 0;                                           // [NPL][RW]
+  static constexpr size_t O_RING = al16(O_TWR + E2 * NPL * RW);                // [M+1][NCHY][TW]
+  static constexpr size_t O_DCR = al16(O_RING + E2 * (M + 1) * NCHY * TW);     // [M+1][NPL][TW]
+  static constexpr size_t O_XW = al16(O_DCR + E2 * (M + 1) * NPL * TW);        // [K+1][M]
+  static constexpr size_t O_XW4 = al16(O_XW + E2 * (K + 1) * M);               // float4 [K+1][M]
   static constexpr size_t O_PBUF = al16(O_XW4 + 16ull * (K + 1) * M);          // float  [TW][PS]
-  static constexpr size_t O_DBUF = al16(O_PBUF + 4ull * TW * PS);              // float2 [2][NPL][TW]
-  static constexpr size_t O_ABUF = al16(O_DBUF + 8ull * 2 * NPL * TW);         // float  [RW][MZ+1]
+  static constexpr size_t O_DBUF = al16(O_PBUF + 4ull * TW * PS);              // [2][NPL][TW]
+  static constexpr size_t O_ABUF = al16(O_DBUF + E2 * 2 * NPL * TW);           // float  [RW][MZ+1]
   static constexpr size_t O_SROW = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [3][SROW]
   static constexpr size_t O_MBAR = al16(O_SROW + 4ull * 3 * SROW);             // uint64 [3]
   static constexpr size_t O_OFFS = al16(O_MBAR + 8ull * 3);                    // float2 [NPL]
@@ -179,15 +189,15 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 
 // Sum of M consecutive lanes' values starting at this lane (lanes + M - 1 <= 31
 // are exact; the rest are unused), by doubling windows.
-template <int M>
-__device__ __forceinline__ float lane_box_sum(float v) {
+template <int M, typename T = float>
+__device__ __forceinline__ T lane_box_sum(T v) {
   static_assert(M < 16, "window");
   const unsigned full = 0xffffffffu;
-  const float s1 = v;
-  const float s2 = s1 + __shfl_down_sync(full, s1, 1);
-  const float s4 = s2 + __shfl_down_sync(full, s2, 2);
-  const float s8 = s4 + __shfl_down_sync(full, s4, 4);
-  float r = 0.f;
+  const T s1 = v;
+  const T s2 = s1 + __shfl_down_sync(full, s1, 1);
+  const T s4 = s2 + __shfl_down_sync(full, s2, 2);
+  const T s8 = s4 + __shfl_down_sync(full, s4, 4);
+  T r = 0;
   int off = 0;
   if (M & 8) { r = s8; off = 8; }
   if (M & 4) { r += off ? __shfl_down_sync(full, s4, off) : s4; off += 4; }
@@ -245,11 +255,14 @@ __device__ __forceinline__ void observer_hann(const float* pa, float2 (&T)[SG<M,
 
 // MODE 0: the plain path (no dump, no features, both compiled out); 1: debug
 // dump of the windowed spectrum and power (features if requested); 2: the
-// learned estimator's features.
-template <int M, int MZ, int MODE>
-__global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const SpecArgs a) {
+// learned estimator's features.  F64: the precision form, spatial sums in
+// double precision (one CTA per SM; the observer, the kz reduction and the
+// smoothed state stay FP32, the power is rounded to FP32 once).
+template <int M, int MZ, int MODE, bool F64 = false>
+__global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_kernel(const SpecArgs a) {
   constexpr bool DUMP = MODE == 1;
-  using G = SG<M, MZ>;
+  using G = SG<M, MZ, F64>;
+  using C2 = typename std::conditional<F64, double2, float2>::type;
   constexpr int K = G::K, J = G::J, NPL = G::NPL, NCHY = G::NCHY;
   constexpr int TW = G::TW, RW = G::RW, NTHR = G::NTHR, PS = G::PS, KPAD = G::KPAD;
   constexpr int NH = G::NH, NH1 = G::NH1, NDT = G::NDT, NTW = G::NTW, NBT = G::NBT, NOB = G::NOB;
@@ -261,13 +274,13 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   const int tid = threadIdx.x, lane = tid & 31;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* twr = reinterpret_cast<float2*>(smem_raw + G::O_TWR);
-  float2* ring = reinterpret_cast<float2*>(smem_raw + G::O_RING);
-  float2* dcr = reinterpret_cast<float2*>(smem_raw + G::O_DCR);
-  float2* xw = reinterpret_cast<float2*>(smem_raw + G::O_XW);
+  C2* twr = reinterpret_cast<C2*>(smem_raw + G::O_TWR);
+  C2* ring = reinterpret_cast<C2*>(smem_raw + G::O_RING);
+  C2* dcr = reinterpret_cast<C2*>(smem_raw + G::O_DCR);
+  C2* xw = reinterpret_cast<C2*>(smem_raw + G::O_XW);
   float4* xw4 = reinterpret_cast<float4*>(smem_raw + G::O_XW4);
   float* pbuf = reinterpret_cast<float*>(smem_raw + G::O_PBUF);
-  float2* dbuf = reinterpret_cast<float2*>(smem_raw + G::O_DBUF);
+  C2* dbuf = reinterpret_cast<C2*>(smem_raw + G::O_DBUF);
   float* abuf = reinterpret_cast<float*>(smem_raw + G::O_ABUF);
   float* srow = reinterpret_cast<float*>(smem_raw + G::O_SROW);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + G::O_MBAR);
@@ -277,15 +290,24 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
   float* ftot = reinterpret_cast<float*>(smem_raw + G::O_FTOT);
   const bool feat = MODE != 0 && a.feat != nullptr;
   if (feat)
-    for (int i = tid; i < G::NBINS; i += NTHR) fgs[i] = a.feat_gather[i];
+    for (int i = tid; i < a.feat_n; i += NTHR) fgs[i] = a.feat_gather[i];
 
   // Power scale (Mz/sqrt(N))^2 and the 1/16 of the 4x Hann taps, as sig^2 on
   // the x-DFT weights and box sums (everything before the power is linear).
   const float sig = sqrtf(float(MZ) / float(16 * M * M));
+  const double sigd = sqrt(double(MZ) / double(16 * M * M));
   for (int i = tid; i < (K + 1) * M; i += NTHR) {
-    const float2 w = cscale(a.tables->xcoef[i / M][i % M], sig);
-    xw[i] = w;                                   // (wr, wi)
-    xw4[i] = make_float4(w.x, w.x, w.y, w.y);    // (wr, wr, wi, wi)
+    if constexpr (F64) {   // Hann(mx) e^{j2pi kx (mx-K)/M} sig, in double
+      const int kx = i / M, mx = i % M;
+      const double hann = 0.5 + 0.5 * cospi(2.0 * (mx - K) / M);
+      double sn, cs;
+      sincospi(2.0 * kx * (mx - K) / M, &sn, &cs);
+      xw[i] = make_double2(hann * cs * sigd, hann * sn * sigd);
+    } else {
+      const float2 w = cscale(a.tables->xcoef[i / M][i % M], sig);
+      xw[i] = w;                                   // (wr, wi)
+      xw4[i] = make_float4(w.x, w.x, w.y, w.y);    // (wr, wr, wi, wi)
+    }
   }
   const float alpha = a.alpha, oma = 1.0f - alpha;
   if (tid == 0) {
@@ -354,6 +376,9 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     float2 YR[K], YI[K], Yc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < K; ++p) { YR[p] = make_float2(0.f, 0.f); YI[p] = make_float2(0.f, 0.f); }
+    double2 Yd[F64 ? M : 1];      // the precision form: the M bins in double (index ky + K)
+#pragma unroll
+    for (int k = 0; k < (F64 ? M : 1); ++k) Yd[k] = make_double2(0.0, 0.0);
 
     auto loadA = [&](int i) {             // prefetch input row i into this lane's abuf slot
       if (athr) {
@@ -388,30 +413,37 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
 #pragma unroll
       for (int p = 0; p < NPL; ++p) {
         const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        const float2 v = csub(Tw[p], offs[p]);
-        twr[p * RW + ua] = real ? make_float2(v.x, v.x) : v;   // real planes as (v, v)
+        if constexpr (F64) {   // exact difference in double
+          const double vx = double(Tw[p].x) - double(offs[p].x), vy = double(Tw[p].y) - double(offs[p].y);
+          twr[p * RW + ua] = real ? make_double2(vx, vx) : make_double2(vx, vy);
+        } else {
+          const float2 v = csub(Tw[p], offs[p]);
+          twr[p * RW + ua] = real ? make_float2(v.x, v.x) : v;   // real planes as (v, v)
+        }
       }
     };
     // whole observer warp: box sums along x of input row i (the (0,0) bin of
     // the row window at column ua), their running sum over the last M rows and
     // a ring of the last M+1 rows' sums
     auto doA2 = [&](int i) {
-      float2 bs[NPL];
+      C2 bs[NPL];
 #pragma unroll
       for (int p = 0; p < NPL; ++p) {
         const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        const float2 v = ua < RW ? twr[p * RW + ua] : make_float2(0.f, 0.f);
+        C2 v;
+        v.x = 0; v.y = 0;
+        if (ua < RW) v = twr[p * RW + ua];
         bs[p].x = lane_box_sum<M>(v.x);
-        bs[p].y = real ? 0.f : lane_box_sum<M>(v.y);
+        bs[p].y = real ? decltype(v.y)(0) : lane_box_sum<M>(v.y);
       }
       if (ua < TW) {
         const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);   // oslot holds row i - M
-        float2* dnew = dbuf + (i & 1) * DC_SLOT;
-        const float2* dold = dbuf + ((i + 1) & 1) * DC_SLOT;
+        C2* dnew = dbuf + (i & 1) * DC_SLOT;
+        const C2* dold = dbuf + ((i + 1) & 1) * DC_SLOT;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
-          const float2 val = cscale(bs[p], sig);
-          float2 run = i > 0 ? cadd(dold[p * TW + ua], val) : val;
+          const C2 val = cscale(bs[p], F64 ? sigd : sig);
+          C2 run = i > 0 ? cadd(dold[p * TW + ua], val) : val;
           if (i >= M) run = csub(run, dcr[oslot * DC_SLOT + p * TW + ua]);
           dcr[slot * DC_SLOT + p * TW + ua] = val;
           dnew[p * TW + ua] = run;
@@ -441,8 +473,42 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     const int TH = y1 - y0;
     auto doB = [&](int i) {               // x-DFT of input row i into ring slot i mod (M+1)
       if (!bthr) return;
-      float2* rs = ring + (i % (M + 1)) * RING_SLOT;
-      if (bg == 0) {                      // real planes, stored (v, v): (wr, wi) x (v, v)
+      C2* rs = ring + (i % (M + 1)) * RING_SLOT;
+      if constexpr (F64) {
+        const double2* w = xw + bkx * M;
+        if (bg == 0) {                    // real planes (stored (v, v))
+          const double2* r0 = twr + bx + 2 * K;
+          const double2* r1 = twr + (NPL - 1) * RW + bx + 2 * K;
+          double2 c0 = make_double2(0.0, 0.0), c1 = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int mx = 0; mx < M; ++mx) {
+            const double2 cw = w[mx];
+            c0.x = fma(cw.x, r0[-mx].x, c0.x);
+            c0.y = fma(cw.y, r0[-mx].x, c0.y);
+            if (EVEN) {
+              c1.x = fma(cw.x, r1[-mx].x, c1.x);
+              c1.y = fma(cw.y, r1[-mx].x, c1.y);
+            }
+          }
+          rs[bkx * TW + bx] = c0;
+          if (EVEN) rs[(G::base(NPL - 1) + bkx) * TW + bx] = c1;
+        } else {                          // complex plane bg: +kx and -kx together
+          const double2* row = twr + bg * RW + bx + 2 * K;
+          double2 ac = make_double2(0.0, 0.0), db = make_double2(0.0, 0.0);
+#pragma unroll
+          for (int mx = 0; mx < M; ++mx) {
+            const double2 cw = w[mx], v = row[-mx];
+            ac.x = fma(cw.x, v.x, ac.x);
+            ac.y = fma(cw.x, v.y, ac.y);
+            db.x = fma(cw.y, v.x, db.x);
+            db.y = fma(cw.y, v.y, db.y);
+          }
+          const int c0 = G::base(bg) + K;
+          rs[(c0 + bkx) * TW + bx] = make_double2(ac.x - db.y, ac.y + db.x);
+          if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_double2(ac.x + db.y, ac.y - db.x);
+        }
+        return;
+      } else if (bg == 0) {               // real planes, stored (v, v): (wr, wi) x (v, v)
         const float2* w = xw + bkx * M;
         const float2* r0 = twr + bx + 2 * K;
         const float2* r1 = twr + (NPL - 1) * RW + bx + 2 * K;
@@ -474,6 +540,44 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     auto doC = [&](int i) {               // y-SDFT, Hann(ky), high-pass, power of row i
       if (!cthr) return;
       const int yo = y0 + i - 2 * K;
+      if constexpr (F64) {                // Y_k <- w_k Y_k + c_k d in double, Hann, correction, power
+        const double2 xn = ring[(i % (M + 1)) * RING_SLOT + tid];
+        double2 d = xn;
+        if (i >= M) d = csub(xn, ring[((i + 1) % (M + 1)) * RING_SLOT + tid]);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const double2 w = c_dw[MI][k], c = c_dc[MI][k], y = Yd[k];
+          const double cr = fma(c.x, d.x, -c.y * d.y), ci = fma(c.x, d.y, c.y * d.x);
+          Yd[k] = make_double2(fma(w.x, y.x, fma(-w.y, y.y, cr)), fma(w.x, y.y, fma(w.y, y.x, ci)));
+        }
+        if (!(i >= 2 * K && yo < y1)) return;
+        const double2 D = dbuf[(i & 1) * DC_SLOT + plc * TW + xy];
+        float* pb = pbuf + xy * PS + cy * M;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const double2 yp = Yd[(k + 1) % M], ym = Yd[(k + M - 1) % M];
+          double zx = fma(2.0, Yd[k].x, yp.x + ym.x), zy = fma(2.0, Yd[k].y, yp.y + ym.y);
+          const double f = k == K ? 2.0 * wxh : ((k == K - 1 || k == K + 1) ? double(wxh) : 0.0);
+          zx -= D.x * f;
+          zy -= D.y * f;
+          const double pw = fma(zx, zx, zy * zy);
+          pb[k] = float(pw);
+          if (DUMP && x0 + xy < W) {
+            const SpecTables& tb = *a.tables;
+            const size_t pix = size_t(yo) * W + x0 + xy;
+            const int izp = plc + J, izm = ((-plc) + J + MZ) % MZ;
+            const double sc = 0.25 * double(MZ) / sqrt(double(M * M * MZ)) / sigd;
+            const float2 u = cmul(tb.uncenter[kxc + K], tb.uncenter[k]);
+            const float2 sv = make_float2(float((double(u.x) * zx - double(u.y) * zy) * sc),
+                                          float((double(u.x) * zy + double(u.y) * zx) * sc));
+            const size_t op = ((pix * MZ + izp) * M + k) * M + (kxc + K);
+            const size_t om = ((pix * MZ + izm) * M + (M - 1 - k)) * M + (K - kxc);
+            a.dump_win[op] = sv;
+            a.dump_win[om] = conjf2(sv);
+            if (a.dump_pow) { a.dump_pow[op] = float(pw); a.dump_pow[om] = float(pw); }
+          }
+        }
+      } else {
       const float2 xn = ring[(i % (M + 1)) * RING_SLOT + tid];
       float2 d = xn;
       if (i >= M) d = csub(xn, ring[((i + 1) % (M + 1)) * RING_SLOT + tid]);
@@ -534,6 +638,7 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
       const float pwc = fmaf(zcx, zcx, zcy * zcy);
       pb[K] = pwc;
       dump(K, zcx, zcy, pwc);
+      }
     };
     auto doD = [&](int i) {               // reduce over kz, smooth (in place in the row ring)
       const int yo = y0 + i - 2 * K, r = i - 2 * K;
@@ -589,7 +694,7 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
           if (lane == 0) ftot[x] = t;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");
-        const int nv = a.feat_ld / 8;
+        const int nv = a.feat_ld / 8, nfeat = a.feat_n;
         for (int task = tid; task < TW * nv; task += NTW) {
           const int x = task / nv, v = task - x * nv;
           if (x0 + x >= W) continue;
@@ -600,8 +705,8 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int b0 = 8 * v + 2 * q;
-            const float f0 = b0 < G::NBINS ? 0.1f * (__log2f(fmaf(pb[fgs[b0]], inv, 1e-6f)) + 10.f) : 0.f;
-            const float f1 = b0 + 1 < G::NBINS ? 0.1f * (__log2f(fmaf(pb[fgs[b0 + 1]], inv, 1e-6f)) + 10.f) : 0.f;
+            const float f0 = b0 < nfeat ? 0.1f * (__log2f(fmaf(pb[fgs[b0]], inv, 1e-6f)) + 10.f) : 0.f;
+            const float f1 = b0 + 1 < nfeat ? 0.1f * (__log2f(fmaf(pb[fgs[b0 + 1]], inv, 1e-6f)) + 10.f) : 0.f;
             const __nv_bfloat162 h2 = __floats2bfloat162_rn(f0, f1);
             packed[q] = *reinterpret_cast<const uint32_t*>(&h2);
           }
@@ -613,22 +718,72 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
     };
 
     // ---- prologue: offsets, observer of row 0, x-DFT of row 0 ----------------
-    if (owarp) loadA(0);
     // Per-plane offset removed from every Tw of this segment before the spatial
     // sums.  The high-passed, Hann-windowed spectrum is exactly invariant to a
     // spatially constant offset per temporal plane (it only feeds the removed
     // kx = ky = 0 bin and the correction that cancels its window leakage), so
     // subtracting one constant per segment leaves the result unchanged while
     // keeping the FP32 sums at the scale of the texture instead of the DC level.
-    if (owarp && ua == 0) {
-      cp_async_wait0();
-      float pa[MZ + 1];
-      for (int f = 0; f <= MZ; ++f) pa[f] = abuf[f];
-      float2 Tn[NPL], Tw0[NPL];
-      observer_hann<M, MZ>(pa, Tn, Tw0);
+    // The constant is the mean of Tw over the segment's first window rows (min(M,
+    // rows) input rows of the TW + 2K columns), so the residual DC that the sums
+    // and the leakage correction carry is the variation of the local mean, not
+    // the full texture amplitude at one pixel.  It is formed as the first
+    // pixel's Tw plus the mean difference from it, which is exactly that pixel's
+    // value when the block is constant (a constant input then leaves exact
+    // zeros in every spatial sum, as the oracle's high-pass does).
+    {
+      // all threads: one pixel (row i, column u) of the block each (at most two)
+      constexpr int NW = NTHR / 32;
+      const int nr0 = min(M, nrows), ntask = nr0 * RW;
+      float2 tw[2][NPL];
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) offs[p] = Tw0[p];
+      for (int r = 0; r < 2; ++r) {
+        const int t = tid + r * NTHR;
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) tw[r][p] = make_float2(0.f, 0.f);
+        if (t < ntask) {
+          const int i = t / RW, u = t - i * RW;
+          const int rs = clampi(y0 - K + i, H), xs = clampi(x0 - K + u, W);
+          const size_t o = size_t(rs) * W + xs, plane = size_t(H) * W;
+          float pa[MZ + 1];
+          pa[0] = a.frame[o];
+#pragma unroll
+          for (int f = 0; f < MZ; ++f) pa[1 + f] = a.obs_old[f * plane + o];
+          float2 Tn[NPL];
+          observer_hann<M, MZ>(pa, Tn, tw[r]);
+        }
+      }
+      if (tid == 0) {
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) offs[p] = tw[0][p];      // the reference: row 0, column 0
+      }
+      __syncthreads();
+      float2* red = reinterpret_cast<float2*>(pbuf);           // [NW][NPL] scratch (pbuf is free here)
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (tid + r * NTHR < ntask) v = cadd(v, csub(tw[r][p], offs[p]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+          v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) red[(tid >> 5) * NPL + p] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const float inv = 1.0f / float(ntask);
+#pragma unroll
+        for (int p = 0; p < NPL; ++p) {
+          float2 v = make_float2(0.f, 0.f);
+          for (int w = 0; w < NW; ++w) v = cadd(v, red[w * NPL + p]);   // fixed order
+          offs[p] = cadd(offs[p], cscale(v, inv));
+        }
+      }
     }
+    if (owarp) loadA(0);
     if (tid == 0) {
       load_row(0);
       if (TH > 1) load_row(1);
@@ -683,11 +838,15 @@ __global__ void __launch_bounds__(SG<M, MZ>::NTHR, 2) spectrum_kernel(const Spec
 template <int M, int MZ>
 cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   using G = SG<M, MZ>;
+  using G64 = SG<M, MZ, true>;
   if (a.tw != G::TW || a.kpad != G::KPAD) return cudaErrorInvalidValue;
-  auto kern = a.dump_win ? spectrum_kernel<M, MZ, 1>
-                         : (a.feat ? spectrum_kernel<M, MZ, 2> : spectrum_kernel<M, MZ, 0>);
+  if (a.f64 && a.feat) return cudaErrorInvalidValue;     // no features in the precision form
+  auto kern = a.f64 ? (a.dump_win ? spectrum_kernel<M, MZ, 1, true> : spectrum_kernel<M, MZ, 0, true>)
+                    : (a.dump_win ? spectrum_kernel<M, MZ, 1>
+                                  : (a.feat ? spectrum_kernel<M, MZ, 2> : spectrum_kernel<M, MZ, 0>));
+  const size_t smem = a.f64 ? G64::SMEM : G::SMEM;
   ResidentShape rs{};
-  cudaError_t e = resident_shape(kern, G::NTHR, G::SMEM, &rs);
+  cudaError_t e = resident_shape(kern, G::NTHR, smem, &rs);
   if (e != cudaSuccess) return e;
   const int nsm = rs.nsm, per_sm = rs.per_sm;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -695,7 +854,7 @@ cudaError_t launch_spec_t(const SpecArgs& a, cudaStream_t st) {
   const long long units = (long long)((a.W + G::TW - 1) / G::TW) * a.H;
   long long grid = (long long)nsm * per_sm;
   if (grid > units) grid = units;
-  kern<<<unsigned(grid), G::NTHR, G::SMEM, st>>>(a);
+  kern<<<unsigned(grid), G::NTHR, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -753,7 +912,18 @@ cudaError_t spectrum_init_constants() {
       rncy[mi][p] = make_float2(-c[mi][p].y, -c[mi][q].y);
     }
   }
+  double2 dw[7][kMaxM] = {}, dc[7][kMaxM] = {};
+  for (int mi = 0; mi < 7; ++mi) {
+    const int M = 2 * mi + 3, K = (M - 1) / 2;
+    for (int i = 0; i < M; ++i) {
+      const int k = i - K;
+      dw[mi][i] = make_double2(std::cos(2 * pi * k / M), std::sin(2 * pi * k / M));
+      dc[mi][i] = make_double2(std::cos(-2 * pi * k * K / M), std::sin(-2 * pi * k * K / M));
+    }
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_rwx, rwx, sizeof(rwx));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dw, dw, sizeof(dw));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dc, dc, sizeof(dc));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rwy, rwy, sizeof(rwy));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rnwy, rnwy, sizeof(rnwy));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcx, rcx, sizeof(rcx));
@@ -781,8 +951,8 @@ int spectrum_threads(int M, int Mz) {
   return 0;
 }
 
-size_t spectrum_smem(int M, int Mz) {
-#define X(m, z) if (M == m && Mz == z) return SG<m, z>::SMEM;
+size_t spectrum_smem(int M, int Mz, bool f64) {
+#define X(m, z) if (M == m && Mz == z) return f64 ? SG<m, z, true>::SMEM : SG<m, z>::SMEM;
   WH_SPEC_CASES(X)
 #undef X
   return 0;

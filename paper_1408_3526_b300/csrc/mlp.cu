@@ -240,10 +240,13 @@ int forward_impl(wh_mlp* m, const void* x, int ldx, int n, bool train) {
 
 // ---------------------------------------------------------------------------
 namespace wh {
+int mlp_n_in(const wh_mlp* m) { return m ? m->n_in : 0; }
+
 // Forward pass enqueued on `st` (the caller's stream) instead of the network's
 // own: the whitening stream's learned search runs it between its spectrum and
 // selection kernels, which must see its input and output in stream order.
 // The network's buffers are shared, so one network serves one caller at a time.
+
 int mlp_forward_on(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy, cudaStream_t st) {
   if (!m || !x || n < 1 || ldx < m->n_in || (ldx % 8)) return WH_EINVAL;
   const cudaStream_t own = m->st;

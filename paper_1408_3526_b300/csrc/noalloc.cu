@@ -133,8 +133,9 @@ extern "C" int wh_push_frame_noalloc(wh_stream* s, const float* frame, int is_de
   sa.obs_old = s->obs[s->cur]; sa.obs_new = s->obs[1 - s->cur]; sa.Astate = s->Astate;
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
-  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
+  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_n = s->feat_n; sa.feat_gather = s->d_fgather;
   sa.err = s->d_err;
+  sa.f64 = s->spec_f64;
   e = launch_spectrum(sa, s->st);
   if (e != cudaSuccess) return wh_cuda_fail(e, "spectrum kernel");
   // 2. autocorrelation search with all scratch in the static array

@@ -54,8 +54,10 @@ struct SStream {
   std::vector<float*> pinned_in;          // one per slot use (ring)
   float* pinned_out = nullptr;
   int ring = 0;
-  bool busy = false;                      // a frame of this stream is on the GPU
+  bool busy = false;                      // a frame of this stream is on the GPU (or its result
+                                          // is still in pinned_out)
   bool closing = false;
+  long long harvest = -1;                 // request whose result waits in pinned_out
 };
 
 }  // namespace
@@ -89,6 +91,10 @@ struct DoneCtx {
   long long req;
 };
 
+// Host callback at the end of a frame's work on its CUDA stream: timestamps
+// the completion.  It copies nothing: with kept results the whitened frame
+// waits in the stream's pinned buffer and the dispatcher thread moves it to
+// the request (outside the lock) before the stream's next frame may reuse it.
 void CUDART_CB on_done(void* p) {
   DoneCtx* c = static_cast<DoneCtx*>(p);
   wh_server* srv = c->srv;
@@ -96,21 +102,47 @@ void CUDART_CB on_done(void* p) {
     std::lock_guard<std::mutex> lk(srv->mu);
     Request& r = srv->reqs[c->req];
     r.done = srv->now();
-    r.finished = true;
     SStream& st = srv->streams[r.stream];
-    st.busy = false;
-    srv->inflight -= 1;
     srv->served += 1;
     srv->pixels_served += (long long)st.h * st.w;
     srv->latencies.push_back(r.done - r.arrival);
     srv->last_done = std::max(srv->last_done, r.done);
     if (srv->keep_results && st.pinned_out) {
-      r.result.assign(st.pinned_out, st.pinned_out + size_t(st.h) * st.w);
+      st.harvest = c->req;
+    } else {
+      r.finished = true;
+      st.busy = false;
+      srv->inflight -= 1;
     }
   }
   srv->cv_work.notify_all();
   srv->cv_done.notify_all();
   delete c;
+}
+
+// Move one finished frame's result from its stream's pinned buffer to the
+// request (called by the dispatcher with the lock held; copies unlocked).
+bool harvest_one(wh_server* srv, std::unique_lock<std::mutex>& lk) {
+  for (auto& kv : srv->streams) {
+    SStream& st = kv.second;
+    if (st.harvest < 0) continue;
+    const long long rid = st.harvest;
+    const float* src = st.pinned_out;
+    const size_t n = size_t(st.h) * st.w;
+    lk.unlock();
+    std::vector<float> res(src, src + n);      // the stream stays busy: nothing rewrites src
+    lk.lock();
+    Request& r = srv->reqs[rid];
+    r.result = std::move(res);
+    r.finished = true;
+    SStream& st2 = srv->streams[r.stream];
+    st2.harvest = -1;
+    st2.busy = false;
+    srv->inflight -= 1;
+    srv->cv_done.notify_all();
+    return true;
+  }
+  return false;
 }
 
 // Oldest waiting frame of a stream that is not on the GPU (FIFO across streams).
@@ -129,6 +161,7 @@ long long pick(wh_server* srv, int* sid) {
 void dispatch_loop(wh_server* srv) {
   std::unique_lock<std::mutex> lk(srv->mu);
   while (!srv->stop) {
+    if (harvest_one(srv, lk)) continue;
     int sid = -1;
     long long rid = -1;
     if (srv->inflight < srv->max_inflight) rid = pick(srv, &sid);
@@ -173,13 +206,31 @@ void dispatch_loop(wh_server* srv) {
 
 extern "C" {
 
-long long wh_stream_device_bytes(int h, int w, int window, int temporal_order, wh_vgrid grid) {
+long long wh_stream_device_bytes_opt(int h, int w, int window, int temporal_order, wh_vgrid grid,
+                                     const wh_params* opt) {
   if (h < 1 || w < 1 || window < 3 || temporal_order < 2 || !(grid.step > 0.f)) return -1;
   const long long npix = (long long)h * w;
   const long long kpad = ((long long)window * window + 3) & ~3LL;
   const long long L = (long long)(2.0 * grid.vmax / grid.step + 1.5);
   // observer ping-pong, smoothed state, frame, whitened/vx/vy/vidx, tables
-  return npix * (2LL * temporal_order * 4 + kpad * 4 + 4 + 16) + L * 64 * 1024 + (1 << 20);
+  long long b = npix * (2LL * temporal_order * 4 + kpad * 4 + 4 + 16) + L * 64 * 1024 + (1 << 20);
+  if (opt) {
+    if (opt->pipeline) b += npix * kpad * 4;                       // second smoothed-state buffer
+    const int prec = opt->precision;
+    if ((prec & 3) || (prec & WH_PREC_TC_SHORTLIST)) {             // tensor-core shortlist scratch
+      const long long kg = ((long long)window * window + 7) & ~7LL;
+      const long long ntile = (L * L + 127) / 128;
+      const long long nc = ntile * 4 > 8 ? ntile * 4 : 8;
+      b += npix * (2 * kg + 4 + 8 * nc) + 2 * ntile * 128 * kg + 4;
+    }
+    if (prec & WH_PREC_TC_SEPARABLE) b += 8192;                    // stage-1 operand
+    if (opt->debug_dump) b += npix * (long long)window * window * temporal_order * 12;
+  }
+  return b;
+}
+
+long long wh_stream_device_bytes(int h, int w, int window, int temporal_order, wh_vgrid grid) {
+  return wh_stream_device_bytes_opt(h, w, window, temporal_order, grid, nullptr);
 }
 
 int wh_server_create(double hbm_budget_bytes, int max_inflight, int queue_limit, int n_cuda_streams,
@@ -209,7 +260,7 @@ int wh_server_create(double hbm_budget_bytes, int max_inflight, int queue_limit,
 int wh_server_open(wh_server* srv, int h, int w, int window, int temporal_order, wh_vgrid grid,
                    const wh_params* opt, int* stream_id) {
   if (!srv || !stream_id) return WH_EINVAL;
-  const long long need = wh_stream_device_bytes(h, w, window, temporal_order, grid);
+  const long long need = wh_stream_device_bytes_opt(h, w, window, temporal_order, grid, opt);
   if (need < 0) return WH_EINVAL;
   int id;
   int cuda_idx;
@@ -286,8 +337,7 @@ int wh_server_wait(wh_server* srv, long long request_id, float* whitened, double
   Request& r = it->second;
   if (latency_s) *latency_s = r.done - r.arrival;
   if (whitened && !r.result.empty()) std::memcpy(whitened, r.result.data(), sizeof(float) * r.result.size());
-  r.result.clear();
-  r.result.shrink_to_fit();
+  srv->reqs.erase(it);              // a request is returned once; the table stays bounded
   return WH_OK;
 }
 

@@ -41,6 +41,10 @@ static int set_cuda_err(cudaError_t e, const char* what) {
   } while (0)
 
 static const double kPi = 3.14159265358979323846;
+// Row-bound widening of the tensor-core separable search per unit of a pixel's
+// sum |Q sums|: TF32 operands (10 explicit mantissa bits, |B| <= 1) bound
+// |T~ - T| by sqrt(2) 1.53 2^-10 per kx row, 4.23e-3 after the sum over kx.
+static const float kTcSepWiden = 4.5e-3f;
 
 char* wh_error_buffer() { return g_err; }
 int wh_cuda_fail(cudaError_t e, const char* what) { return set_cuda_err(e, what); }
@@ -151,6 +155,7 @@ __global__ void accumulate_count_kernel(const int* n, long long* total) { *total
 
 namespace wh {
 int mlp_forward_on(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy, cudaStream_t st);
+int mlp_n_in(const wh_mlp* m);
 }
 
 static int learned_search(wh_stream* s) {
@@ -225,7 +230,7 @@ static void free_stream(wh_stream* s) {
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
                   s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
                   s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather, s->d_ymlp,
-                  s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list};
+                  s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list, s->d_bop};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -273,7 +278,8 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   if (p.band > K || p.delay_z >= Mz || p.alpha >= 1.0) return WH_EINVAL;
   if (!spectrum_supported(M, Mz)) return WH_EUNSUP;
   const int pmode = p.precision & 3;
-  if (p.precision & ~(3 | WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST)) return WH_EUNSUP;
+  if (p.precision & ~(3 | WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST | WH_PREC_TC_SEPARABLE | WH_PREC_SPEC_F64))
+    return WH_EUNSUP;
   if (pmode == 3) return WH_EINVAL;
   if (pmode != 0 && !autocorr_tc_supported(M)) return WH_EUNSUP;
 
@@ -286,11 +292,16 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->d_raw = nullptr; s->d_rs = nullptr; s->prof = 0; s->ev_used = 0; s->t = 0; s->cur = 0;
   s->d_a16 = nullptr; s->d_l1 = nullptr; s->d_cval = nullptr; s->d_cidx = nullptr;
   s->d_table = nullptr; s->d_err = nullptr; s->d_nfb = nullptr;
-  s->d_feat = nullptr; s->feat_ld = 0; s->d_fgather = nullptr; s->mlp = nullptr; s->conf_thr = 0.8f;
+  s->d_feat = nullptr; s->feat_ld = 0; s->feat_n = 0; s->feat_mode = 0; s->d_fgather = nullptr; s->mlp = nullptr;
+  s->conf_thr = 0.8f;
   s->d_ymlp = nullptr; s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
   s->mlp_frames = 0;
   s->as = nullptr;
   s->d_det = nullptr; s->det_bytes = 0; s->d_det_list = nullptr; s->det_list_cap = 0;
+  s->d_bop = nullptr;
+  s->spec_f64 = (p.precision & WH_PREC_SPEC_F64) ? 1 : 0;
+  s->use_tcsep = pmode == 0 && !(p.precision & (WH_PREC_TC_SHORTLIST | WH_PREC_CUDA_CORES)) &&
+                 (p.precision & WH_PREC_TC_SEPARABLE) && autocorr_tcsep_supported(M, L);
   s->tc_mode = pmode == 0 ? 0 : 1;
   s->tc_bf16 = pmode == 2 ? 1 : 0;
   s->use_tc = (pmode != 0) || ((p.precision & WH_PREC_TC_SHORTLIST) && autocorr_tc_supported(M));
@@ -397,6 +408,17 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
       free_stream(s);
       return rc;
     }
+  if (s->use_tcsep) {
+    std::vector<float> bop(2048);
+    build_tcsep_operand(M, L, s->vstep, bop.data());
+    alloc((void**)&s->d_bop, sizeof(float) * bop.size());
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_bop, bop.data(), sizeof(float) * bop.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "tensor-core search operand");
+      free_stream(s);
+      return rc;
+    }
+  }
   if (s->use_tc) {
     alloc((void**)&s->d_a16, 2 * npix * s->kg);
     alloc((void**)&s->d_l1, sizeof(float) * npix);
@@ -451,7 +473,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
       }
   }
   // the spectrum kernel's shared memory must fit one CTA
-  if (spectrum_threads(M, Mz) <= 0 || spectrum_smem(M, Mz) > 227 * 1024) {
+  if (spectrum_threads(M, Mz) <= 0 || spectrum_smem(M, Mz, s->spec_f64 != 0) > 227 * 1024) {
     free_stream(s);
     return WH_EUNSUP;
   }
@@ -548,8 +570,9 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
   sa.Astate_out = s->pipeline ? s->Astate_alt : nullptr;
   sa.tables = s->d_spec; sa.hgather = s->d_hgather;
   sa.dump_win = s->d_dump_win; sa.dump_pow = s->d_dump_pow;
-  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_gather = s->d_fgather;
+  sa.feat = s->d_feat; sa.feat_ld = s->feat_ld; sa.feat_n = s->feat_n; sa.feat_gather = s->d_fgather;
   sa.err = s->d_err;
+  sa.f64 = s->spec_f64;
   cudaError_t e = launch_spectrum(sa, ss);
   if (e != cudaSuccess) return set_cuda_err(e, "spectrum kernel");
   if (ev) WH_CU(cudaEventRecord(ev[1], ss));
@@ -579,6 +602,13 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
     if (rc == WH_OK && (e = launch_autocorr_rerank(ta, sp)) != cudaSuccess)
       rc = set_cuda_err(e, "autocorrelation re-rank kernel");
     nlaunch = 5;
+  } else if (s->use_tcsep) {
+    TcSepArgs ta{};
+    ta.npix = s->H * s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad;
+    ta.vmax = float(s->vmax); ta.vstep = float(s->vstep); ta.wcoef = kTcSepWiden;
+    ta.Astate = s->Astate; ta.vidx = s->vidx; ta.vx = s->vx; ta.vy = s->vy;
+    ta.bop = s->d_bop; ta.tab_x = s->d_tabx; ta.err = s->d_err;
+    if ((e = launch_autocorr_tcsep(ta, sp)) != cudaSuccess) rc = set_cuda_err(e, "tensor-core search kernel");
   } else {
     AutocorrArgs aa{};
     aa.H = s->H; aa.W = s->W; aa.M = s->M; aa.L = s->L; aa.kpad = s->kpad;
@@ -848,15 +878,16 @@ int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
 }
 
 int wh_stream_set_features(wh_stream* s, int enable) {
-  if (!s) return WH_EINVAL;
-  if (!enable) {
-    if (s->mlp) return WH_EINVAL;
+  if (!s || enable < 0 || enable > 2) return WH_EINVAL;
+  if (s->d_feat && enable == s->feat_mode) return WH_OK;
+  if (s->d_feat || !enable) {
+    if (s->mlp) return WH_EINVAL;          // the learned mode reads the current layout
     if (s->d_feat) cudaFree(s->d_feat);
     if (s->d_fgather) cudaFree(s->d_fgather);
-    s->d_feat = nullptr; s->d_fgather = nullptr; s->feat_ld = 0;
-    return WH_OK;
+    s->d_feat = nullptr; s->d_fgather = nullptr; s->feat_ld = 0; s->feat_n = 0; s->feat_mode = 0;
+    if (!enable) return WH_OK;
   }
-  if (s->d_feat) return WH_OK;
+  if (s->spec_f64) return WH_EUNSUP;     // the precision form writes no features
   const int M = s->M, K = s->K, Mz = s->Mz, J = (Mz - 1) / 2;
   const bool even = (Mz % 2) == 0;
   const int npl = J + 1 + (even ? 1 : 0), nb = M * M * Mz;
@@ -887,10 +918,25 @@ int wh_stream_set_features(wh_stream* s, int enable) {
         }
         fg[(iz * M + iy) * M + ix] = chan(kz, kx) * M + (ky + K);
       }
-  s->feat_ld = (nb + 7) / 8 * 8;
+  if (enable == 2) {   // one feature per mirror pair (P(-k) = P(k)): bins not after their mirror
+    std::vector<int> uniq;
+    for (int iz = 0; iz < Mz; ++iz)
+      for (int iy = 0; iy < M; ++iy)
+        for (int ix = 0; ix < M; ++ix) {
+          int kzm = -(iz - J);
+          if (kzm < -J) kzm += Mz;
+          const int b = (iz * M + iy) * M + ix, bm = ((kzm + J) * M + (2 * K - iy)) * M + (2 * K - ix);
+          if (b <= bm) uniq.push_back(fg[b]);
+        }
+    fg.swap(uniq);
+  }
+  const int nf = int(fg.size());
+  s->feat_n = nf;
+  s->feat_mode = enable;
+  s->feat_ld = (nf + 7) / 8 * 8;
   cudaError_t e = cudaMalloc(&s->d_feat, 2 * size_t(s->H) * s->W * s->feat_ld);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_fgather, sizeof(int) * nb);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_fgather, fg.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_fgather, sizeof(int) * nf);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_fgather, fg.data(), sizeof(int) * nf, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->d_feat, 0, 2 * size_t(s->H) * s->W * s->feat_ld);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? WH_ENOMEM : set_cuda_err(e, "features");
   return WH_OK;
@@ -910,7 +956,14 @@ int wh_stream_set_learned(wh_stream* s, wh_mlp* mlp, float conf_threshold) {
     s->mlp = nullptr;
     return WH_OK;
   }
-  int rc = wh_stream_set_features(s, 1);
+  // the feature layout the network takes: every bin, or one per mirror pair
+  const int n_in = wh::mlp_n_in(mlp), nb = s->M * s->M * s->Mz;
+  int mode = 0;
+  if (n_in == nb) mode = 1;
+  else if (n_in == (nb + 2 - (s->Mz % 2)) / 2) mode = 2;
+  if (!mode) return WH_EINVAL;
+  s->mlp = nullptr;
+  int rc = wh_stream_set_features(s, mode);
   if (rc != WH_OK) return rc;
   const size_t npix = size_t(s->H) * s->W;
   cudaError_t e = cudaSuccess;

@@ -41,10 +41,16 @@ struct wh_stream {
   void* d_table;
   int* d_err;
   int* d_nfb;
+  // autocorrelation search with the separable stage on tensor cores
+  int use_tcsep;
+  int spec_f64;          // the precision form of the spectrum kernel (spatial sums in double)
+  float* d_bop;          // its stage-1 operand (2048 floats)
   // learned-estimator features and learned velocity mode
   void* d_feat;          // BF16 [H*W][feat_ld]
   int feat_ld;
-  int* d_fgather;        // [M*M*Mz]
+  int feat_n;            // features per pixel: M*M*Mz (mode 1) or one per mirror pair (mode 2)
+  int feat_mode;
+  int* d_fgather;        // [feat_n]
   struct wh_mlp* mlp;    // not owned
   float conf_thr;
   float* d_ymlp;         // [H*W][3]

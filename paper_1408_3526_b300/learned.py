@@ -1,8 +1,9 @@
 """Learned velocity estimator: network front end, training and evaluation.
 
-The network (C ABI wh_mlp_*) maps each pixel's log-power spectrum (all
-M x M x Mz bins of the high-passed, Hann-windowed power, normalised by its
-sum; input (log2(P/sum P + 1e-6) + 10)/10) to (vx, vy, confidence).  It is trained on velocities produced by the
+The network (C ABI wh_mlp_*) maps each pixel's log-power spectrum (the
+high-passed, Hann-windowed power normalised by its sum, input
+(log2(P/sum P + 1e-6) + 10)/10, one value per mirror pair of bins since
+P(-k) = P(k): 676 inputs at 15 x 15 x 6) to (vx, vy, confidence).  It is trained on velocities produced by the
 plain autocorrelation search of this library, and in a stream's learned mode
 replaces that search wherever its confidence reaches a threshold (0.8 by
 default); every other pixel still runs the exact search.  All arithmetic runs
@@ -96,11 +97,41 @@ class MLP:
         return list(st) if st is not None else None
 
 
+def n_features(M, Mz, folded=True):
+    """Network input width: all M*M*Mz bins, or one per mirror pair (P(-k) = P(k))."""
+    nb = M * M * Mz
+    return (nb + 2 - Mz % 2) // 2 if folded else nb
+
+
+def fold_first_layer(W1, M, Mz):
+    """Columns of a first layer over all bins ([h1][M*M*Mz], order [kz][ky][kx])
+    summed over mirror pairs, in the folded input order: the bins k whose flat
+    index is not larger than that of -k.  A network with the folded layer on
+    the folded features computes exactly what the original computes on all bins."""
+    W1 = np.asarray(W1)
+    K, J = (M - 1) // 2, (Mz - 1) // 2
+    cols = []
+    for iz in range(Mz):
+        for iy in range(M):
+            for ix in range(M):
+                kzm = -(iz - J)
+                if kzm < -J:
+                    kzm += Mz
+                b = (iz * M + iy) * M + ix
+                bm = ((kzm + J) * M + (2 * K - iy)) * M + (2 * K - ix)
+                if b < bm:
+                    cols.append(W1[:, b] + W1[:, bm])
+                elif b == bm:
+                    cols.append(W1[:, b])
+    return np.stack(cols, axis=1)
+
+
 def generate_training_data(n_scenes=300, frames=12, H=512, W=640, M=15, Mz=6, vmax=3.0, step=0.25,
-                           samples=2_000_000, seed0=100, vlim=1.75):
+                           samples=2_000_000, seed0=100, vlim=1.75, folded=True):
     """Scenes -> plain GPU path -> (features, labels) at uniformly sampled
     interior pixels of each scene's last frame.  Returns CUDA tensors
-    X bf16 [samples][ld] and V float32 [samples][2]."""
+    X bf16 [samples][ld] and V float32 [samples][2].  folded: one feature per
+    mirror pair of bins (wh_stream_set_features mode 2), else all bins."""
     torch = _torch()
     from .stream import WhitenStream
     per = int(math.ceil(samples / n_scenes))
@@ -110,7 +141,7 @@ def generate_training_data(n_scenes=300, frames=12, H=512, W=640, M=15, Mz=6, vm
     for frames_np, _ in scenes.training_scene_set(n_scenes, frames, H, W, seed0=seed0, vlim=vlim):
         fd = torch.from_numpy(frames_np).cuda()
         with WhitenStream(H, W, M, Mz, vmax, step) as s:
-            check(s.lib.wh_stream_set_features(s._s, 1), "set_features")
+            check(s.lib.wh_stream_set_features(s._s, 2 if folded else 1), "set_features")
             for t in range(frames):
                 s.push(fd[t])
             ld = C.c_int()
@@ -248,14 +279,18 @@ def main(argv=None):
     ap.add_argument("--modes", default="plain,learned", help="comma list of plain, learned")
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--all-bins", action="store_true",
+                    help="input every M*M*Mz bin (1350) instead of one per mirror pair (676)")
     a = ap.parse_args(argv)
-    net = MLP(1350, 256, 128, 3, seed=1)
+    folded = not a.all_bins
+    net = MLP(n_features(15, 6, folded), 256, 128, 3, seed=1)
     if a.load:
         net.load(a.load)
         training = {"loaded": a.load}
     else:
         t0 = time.time()
-        X, V = generate_training_data(n_scenes=a.train_scenes, frames=a.train_frames, samples=a.samples)
+        X, V = generate_training_data(n_scenes=a.train_scenes, frames=a.train_frames, samples=a.samples,
+                                      folded=folded)
         t_data = time.time() - t0
         t0 = time.time()
         hist = train(net, X, V, epochs=a.epochs, lr=1e-3, log=print)
@@ -272,7 +307,8 @@ def main(argv=None):
                               modes=tuple(m for m in a.modes.split(",") if m))
     rep["training"] = training
     rep["eval"] = {"frames": a.eval_frames, "size": [a.eval_h, a.eval_w], "window": 15, "order": 6,
-                   "grid": "+-3 step 0.25", "confidence_threshold": a.conf}
+                   "grid": "+-3 step 0.25", "confidence_threshold": a.conf,
+                   "network_inputs": net.n_in, "inputs": "one per mirror pair" if folded else "all bins"}
     print(json.dumps(rep))
     if a.out:
         with open(a.out, "w") as f:

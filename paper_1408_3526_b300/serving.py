@@ -28,10 +28,11 @@ class Server:
         self._s = h
         self.shapes = {}
 
-    def open(self, h, w, window, order, vmax, step, precision=0):
+    def open(self, h, w, window, order, vmax, step, precision=0, pipeline=False):
         p = _abi.wh_params()
         check(self.lib.wh_default_params(window, order, C.byref(p)), "defaults")
         p.precision = precision
+        p.pipeline = int(bool(pipeline))
         sid = C.c_int()
         rc = self.lib.wh_server_open(self._s, h, w, window, order, _abi.wh_vgrid(vmax, step), C.byref(p),
                                      C.byref(sid))

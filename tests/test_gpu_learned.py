@@ -39,7 +39,7 @@ def _bf16_params(p, n_in, h1, h2):
     return omlp.pack([_bf16_round(W1), b1, _bf16_round(W2), b2, _bf16_round(W3), b3])
 
 
-@pytest.mark.parametrize("n_in,h1,h2", [(1350, 256, 128), (324, 64, 32)])
+@pytest.mark.parametrize("n_in,h1,h2", [(1350, 256, 128), (676, 256, 128), (324, 64, 32)])
 def test_mlp_forward_matches_oracle(n_in, h1, h2):
     import torch
     net, p = _net_with_random_params(n_in, h1, h2, 3)
@@ -89,14 +89,31 @@ def test_mlp_gradients_match_oracle():
     net.close()
 
 
-def test_features_match_oracle_power():
+def _unique_bins(M, Mz):
+    """Flat [kz][ky][kx] indices of the bins not after their mirror -k."""
+    K, J = (M - 1) // 2, (Mz - 1) // 2
+    out = []
+    for iz in range(Mz):
+        kzm = -(iz - J)
+        if kzm < -J:
+            kzm += Mz
+        for iy in range(M):
+            for ix in range(M):
+                b = (iz * M + iy) * M + ix
+                if b <= ((kzm + J) * M + (2 * K - iy)) * M + (2 * K - ix):
+                    out.append(b)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("mode", [1, 2], ids=["all_bins", "one_per_mirror_pair"])
+def test_features_match_oracle_power(mode):
     import torch
 
     from paper_1408_3526_b300.stream import WhitenStream
     M, Mz, T, H, W = 9, 4, 8, 24, 30
     sc = scenes.small_scene(T=T, H=H, W=W, seed=8, tex_size=128)
     with WhitenStream(H, W, M, Mz, 2.0, 0.25) as s:
-        assert s.lib.wh_stream_set_features(s._s, 1) == 0
+        assert s.lib.wh_stream_set_features(s._s, mode) == 0
         fd = torch.from_numpy(sc.frames).cuda()
         for t in range(T):
             s.push(fd[t])
@@ -107,7 +124,10 @@ def test_features_match_oracle_power():
         f = feat.float().cpu().numpy()
     P = oracle.Oracle(M, Mz, 2.0, 0.25).run(sc.frames, spec_frames=[T - 1], power=True)["power"][0]
     ref = omlp.features_from_power(P).reshape(H * W, -1)
-    nb = M * M * Mz
+    if mode == 2:
+        ref = ref[:, _unique_bins(M, Mz)]
+        assert ref.shape[1] == (M * M * Mz + 2) // 2
+    nb = ref.shape[1]
     assert np.all(f[:, nb:] == 0)
     err = np.abs(f[:, :nb] - ref)
     assert np.max(err - (2.0 ** -7) * np.abs(ref)) <= 2e-3, np.max(err)
@@ -126,7 +146,7 @@ def test_training_gains_and_learned_mode():
     M, Mz, vmax, step = 9, 4, 2.0, 0.25
     X, V = learned.generate_training_data(n_scenes=240, frames=10, H=64, W=64, M=M, Mz=Mz, vmax=vmax,
                                           step=step, samples=240_000, seed0=200)
-    n_in = M * M * Mz
+    n_in = learned.n_features(M, Mz)          # one input per mirror pair of bins
     trained = learned.MLP(n_in, 256, 128, 3, seed=1)
     untrained = learned.MLP(n_in, 256, 128, 3, seed=1)
     hist = learned.train(trained, X, V, vstep=step, epochs=30, batch=4096, lr=2e-3)

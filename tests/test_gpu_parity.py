@@ -66,14 +66,17 @@ def test_parity_paper_simulation():
     workload: 25 sinusoids translating between grid points, an occluding
     truncated target, 64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2/4."""
     sc = scenes.paper_sim_scene(T=32)
-    # Its clutter energy sits mostly in the DC bin that the high-pass removes,
-    # so the windowed bins are small next to the raw-scale FP32 sums they come
-    # from: the windowed spectrum is held to 2e-4 of its own RMS here (the raw
-    # spectrum keeps 1e-4; the error against the raw spectrum's RMS is printed).
-    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), win_tol=2 * P.SPEC_TOL)
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31))
 
 
-@pytest.mark.parametrize("precision", [16, 0, 32], ids=["tc_shortlist_rerank", "cuda_cores", "tc_separable"])
+def test_parity_paper_simulation_precision_form():
+    """The same with the spatial sums in double (WH_PREC_SPEC_F64)."""
+    sc = scenes.paper_sim_scene(T=32)
+    _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), precision=64)
+
+
+@pytest.mark.parametrize("precision", [16, 0, 32, 64 | 32],
+                         ids=["tc_shortlist_rerank", "cuda_cores", "tc_separable", "f64_sums_tc_separable"])
 def test_parity_config1_full(precision):
     """64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2 step 1/4 (in full),
     with both FP32-exact engines of the autocorrelation search."""

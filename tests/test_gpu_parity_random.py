@@ -39,13 +39,13 @@ def _cases(n=10, seed=2024):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 16], ids=["cuda_cores", "tc_shortlist_rerank"])
+@pytest.mark.parametrize("precision", [0, 16, 32], ids=["cuda_cores", "tc_shortlist_rerank", "tc_separable"])
 @pytest.mark.parametrize("i,M,Mz,vmax,step,H,W,vx,vy", _cases(),
                          ids=lambda v: str(v) if isinstance(v, int) else None)
 def test_parity_random_shape(i, M, Mz, vmax, step, H, W, vx, vy, precision):
-    """Both FP32-exact search engines (the tensor-core one takes grids up to
-    25 points per axis)."""
-    if precision and 2 * vmax / step + 1 > 25:
+    """The three FP32-exact search engines (the tensor-core shortlist takes
+    grids up to 25 points per axis)."""
+    if precision == 16 and 2 * vmax / step + 1 > 25:
         pytest.skip("tensor-core search: grid longer than 25")
     T = 8
     sc = scenes.small_scene(T=T, H=H, W=W, seed=100 + i, vx=vx, vy=vy, tex_size=128)

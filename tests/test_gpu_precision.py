@@ -1,5 +1,7 @@
 """Precision study (needs a B300): the autocorrelation contraction in F16 and
-BF16 on tensor cores, and the FP32-exact engines, against the FP64 oracle.
+BF16 on tensor cores, the FP32-exact engines (CUDA cores, tensor-core
+shortlist, tensor-core separable), and the precision form of the spectrum
+(spatial sums in double), against the FP64 oracle.
 
 1024 x 1280 frames of the uniform-flow scene generator, 15 x 15 window,
 temporal order 6, velocity grid +-2 step 1/4.  Reported per output:
@@ -26,7 +28,8 @@ from tests import _parity as P
 pytestmark = pytest.mark.gpu
 
 M, MZ, VMAX, VSTEP = 15, 6, 2.0, 0.25
-MODES = {"fp32_exact_tc": 16, "fp32_cuda_cores": 0, "tc_fp16": 1, "tc_bf16": 2}
+MODES = {"fp32_exact_tc": 16, "fp32_cuda_cores": 8, "fp32_exact_tc_separable": 32, "tc_fp16": 1, "tc_bf16": 2,
+         "f64_spatial_sums": 64 | 32}
 
 
 def _run_full(frames, precision):
@@ -113,13 +116,19 @@ def test_precision_study_config3():
     # error, early and at the last frame (the deadbeat observer does not drift)
     crop = np.ascontiguousarray(fr[:, 496:528, 620:660])
     sf = (39, T - 1)
-    g = P.run_gpu(crop, M, MZ, VMAX, VSTEP, spec_frames=sf, debug=True)
-    ref = o.run(crop, spec_frames=list(sf), spectrum=True, windowed=True)
-    for n, t in enumerate(sf):
-        tag = "early" if n == 0 else "last"
-        report[f"spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][n])
-        report[f"spectrum_rel_err_rms_{tag}"] = P.spectrum_rel_err_rms(g["spectrum"][t], ref["spectrum"][n])
-        report[f"windowed_spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["windowed"][t], ref["windowed"][n])
+    ref = o.run(crop, spec_frames=list(sf), spectrum=True, windowed=True, power=True)
+    for pre, prec in (("", 0), ("f64_", 64)):
+        g = P.run_gpu(crop, M, MZ, VMAX, VSTEP, spec_frames=sf, debug=True, precision=prec)
+        for n, t in enumerate(sf):
+            tag = "early" if n == 0 else "last"
+            report[f"{pre}spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["spectrum"][t], ref["spectrum"][n])
+            report[f"{pre}spectrum_rel_err_rms_{tag}"] = P.spectrum_rel_err_rms(g["spectrum"][t],
+                                                                                ref["spectrum"][n])
+            report[f"{pre}windowed_spectrum_rel_err_{tag}"] = P.spectrum_rel_err(g["windowed"][t],
+                                                                                 ref["windowed"][n])
+            report[f"{pre}windowed_spectrum_rel_err_rms_{tag}"] = P.spectrum_rel_err_rms(g["windowed"][t],
+                                                                                         ref["windowed"][n])
+            report[f"{pre}power_rel_err_{tag}"] = P.spectrum_rel_err(g["power"][t], ref["power"][n])
     report["spectrum_rel_err"] = max(report["spectrum_rel_err_early"], report["spectrum_rel_err_last"])
     report["frames"] = T
     report["sampled_pixels"] = len(pts)
@@ -128,7 +137,7 @@ def test_precision_study_config3():
     if out:
         with open(out, "w") as f:
             json.dump(report, f, indent=1)
-    for name in ("fp32_exact_tc", "fp32_cuda_cores"):
+    for name in ("fp32_exact_tc", "fp32_cuda_cores", "fp32_exact_tc_separable", "f64_spatial_sums"):
         r = report[name]
         assert r["velocity_identical_first_half"] >= 0.999
         assert r["velocity_identical_second_half"] >= 0.999
@@ -139,6 +148,9 @@ def test_precision_study_config3():
     for name in ("tc_fp16", "tc_bf16"):
         assert report[name]["whitened_max_err_over_rms_second_half"] <= 1e-3
     assert report["spectrum_rel_err"] <= 1e-4
+    assert report["f64_windowed_spectrum_rel_err_last"] <= 1e-4
+    # the precision form removes the FP32 rounding of the spatial sums
+    assert report["f64_windowed_spectrum_rel_err_last"] < report["windowed_spectrum_rel_err_last"]
 
 
 def test_long_columns_error_bounded():

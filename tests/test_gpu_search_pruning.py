@@ -8,6 +8,10 @@ reading the velocity before and after it compares the two on identical
 inputs.  The full result is also checked against the dumped R: its flat index
 is the lowest one holding the maximum.
 
+Both pruned engines are covered: the CUDA-core search and the tensor-core
+separable search (WH_PREC_TC_SEPARABLE), whose row bounds come from a TF32
+tensor-core product widened by its rigorous error bound.
+
 Scenes cover structured spectra (texture under flow, the paper's sinusoids,
 an impulse), flat spectra (white noise: weak pruning), an all-tie state
 (constant frames: R = 0 everywhere) and a non-finite state (a NaN frame: the
@@ -52,13 +56,17 @@ def _lowest_argmax(R):
     return np.argmax(flat, axis=-1)      # numpy returns the first occurrence
 
 
+@pytest.mark.parametrize("precision", [0, 32], ids=["cuda_cores", "tc_separable"])
 @pytest.mark.parametrize("kind", ["flow", "paper_sim", "noise", "constant", "impulse", "nan"])
 @pytest.mark.parametrize("M,Mz,vmax,step", [(15, 6, 3.0, 0.25), (9, 4, 2.0, 0.25), (7, 5, 3.75, 0.25),
                                              (15, 6, 3.75, 0.25)])
-def test_pruned_search_equals_full_evaluation(kind, M, Mz, vmax, step):
+def test_pruned_search_equals_full_evaluation(kind, M, Mz, vmax, step, precision):
+    """Both pruned engines: the CUDA-core search (exact row bounds) and the
+    tensor-core separable search (row bounds from the TF32 product, widened by
+    its error bound): the velocity equals the full FP32 evaluation's bit for bit."""
     T, H, W = 10, 24, 40
     frames = _frames(kind, T, H, W)
-    with WhitenStream(H, W, M, Mz, vmax, step) as s:
+    with WhitenStream(H, W, M, Mz, vmax, step, precision=precision) as s:
         for t in range(T):
             s.push(frames[t])
             if t < 1:

@@ -73,3 +73,36 @@ def test_back_pressure_sheds_when_a_stream_queue_is_full():
         st = srv.stats()
         assert st["shed"] >= 1 and st["shed"] + st["served"] == 20
         assert sum(r is None for r in got) == st["shed"]
+
+
+def test_admission_charges_the_stream_parameters():
+    """A stream with the frame pipeline (a second smoothed-state buffer) is
+    refused at a budget that admits the serial stream of the same shape."""
+    import ctypes as C
+
+    from paper_1408_3526_b300.serving import Server
+    lib = _abi.load()
+    g = _abi.wh_vgrid(3.0, 0.25)
+    serial = lib.wh_stream_device_bytes(256, 320, 15, 6, g)
+    p = _abi.wh_params()
+    assert lib.wh_default_params(15, 6, C.byref(p)) == 0
+    p.pipeline = 1
+    piped = lib.wh_stream_device_bytes_opt(256, 320, 15, 6, g, C.byref(p))
+    assert piped >= serial + 256 * 320 * 228 * 4
+    with Server(budget_bytes=serial + 1, max_inflight=1, queue_limit=1, n_cuda_streams=1) as srv:
+        assert srv.open(256, 320, 15, 6, 3.0, 0.25, pipeline=True) is None
+        assert srv.open(256, 320, 15, 6, 3.0, 0.25) is not None
+
+
+def test_requests_are_forgotten_once_returned():
+    """The request table stays bounded: a request id is returned once."""
+    from paper_1408_3526_b300.serving import Server
+    fr = scenes.small_scene(T=3, H=48, W=64, seed=9, tex_size=128).frames
+    with Server(budget_bytes=2e9, max_inflight=2, queue_limit=4, n_cuda_streams=1, keep_results=True) as srv:
+        s = srv.open(48, 64, 9, 4, 2.0, 0.25)
+        rids = [srv.submit(s, fr[t], srv.now()) for t in range(3)]
+        for r in rids:
+            e, lat = srv.wait(r, s)
+            assert e.shape == (48, 64) and lat >= 0
+        with pytest.raises(Exception):
+            srv.wait(rids[0], s)

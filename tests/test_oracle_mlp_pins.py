@@ -164,3 +164,33 @@ def test_elementwise_bounds_catch_planted_mistakes():
     g3[sl["W2"]] = gw2.ravel()
     for gm in (g1, g2, g3):
         assert np.any(np.abs(gm - g) > 2 * e)
+
+
+def test_folded_first_layer_equals_network_on_all_bins():
+    """One input per mirror pair: with P(-k) = P(k) (the oracle's power of a real
+    input, pin P8), a first layer whose columns of k and -k are summed gives
+    the same pre-activations on the folded features as the original layer on
+    all bins; the folded width is (M^2 Mz + 2 - Mz % 2) / 2."""
+    import oracle
+    from paper_1408_3526_b300 import learned, scenes
+    for M, Mz in ((5, 4), (5, 3)):
+        sc = scenes.small_scene(T=6, H=7, W=9, seed=11, tex_size=64)
+        P = oracle.Oracle(M, Mz, 1.0, 0.25).run(sc.frames, spec_frames=[5], power=True)["power"][0]
+        f_all = mlp.features_from_power(P).reshape(7 * 9, -1)
+        rng = np.random.default_rng(M * 10 + Mz)
+        W1 = rng.normal(0, 1, (16, M * M * Mz))
+        Wf = learned.fold_first_layer(W1, M, Mz)
+        assert Wf.shape[1] == learned.n_features(M, Mz) == (M * M * Mz + 2 - Mz % 2) // 2
+        K, J = (M - 1) // 2, (Mz - 1) // 2
+        keep = []
+        for iz in range(Mz):
+            kzm = -(iz - J)
+            kzm += Mz if kzm < -J else 0
+            for iy in range(M):
+                for ix in range(M):
+                    b = (iz * M + iy) * M + ix
+                    if b <= ((kzm + J) * M + (2 * K - iy)) * M + (2 * K - ix):
+                        keep.append(b)
+        z_all = f_all @ W1.T
+        z_fold = f_all[:, keep] @ Wf.T
+        assert np.allclose(z_all, z_fold, rtol=1e-12, atol=1e-9)
