@@ -59,6 +59,9 @@ PROFILE_OF = {
     "autocorr_argmax": ("profiles/autocorr_512x640_m15.md", ["k_autocorr.cu", "ac_common.cuh", "common.cuh"]),
     "pef": ("profiles/pef_512x640_m15_mz6.md", ["k_pef.cu", "common.cuh"]),
 }
+# the search kernel's summary when the tensor-core separable engine runs (--precision 32)
+PROFILE_OF_TCSEP = ("profiles/autocorr_tcsep_512x640_m15.md",
+                    ["k_autocorr_tcsep.cu", "ac_common.cuh", "common.cuh", "tc_ptx.cuh"])
 
 
 def kernel_source_sha256(files):
@@ -304,6 +307,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if (args.precision & 32) and not (args.precision & (16 | 3)):
+        PROFILE_OF["autocorr_argmax"] = PROFILE_OF_TCSEP
 
     import torch
     import torch.distributed as dist
