@@ -167,3 +167,47 @@ def test_parity_full_size_config2_sampled():
     print(f"\n[parity 512x640 sampled] velocity identical {same}/{n}, whitened vs oracle {wmax:.2e} xRMS",
           flush=True)
     assert same >= P.VEL_EXACT_FRAC * n
+
+
+@pytest.mark.parametrize("H,W", [(4096, 4096), (8, 65536), (65536, 8)],
+                         ids=["4096x4096", "8x65536", "65536x8"])
+def test_parity_large_and_extreme_shapes(H, W):
+    """A 4096 x 4096 frame (16.8 M pixels, ~17 GB of state) and extreme aspect
+    ratios (a single strip 65536 rows tall: many 256-row restarts of the
+    y-recursion; 8 rows by 65536 columns: thousands of strips) at 15 x 15 /
+    order 6 / grid +-3, against the oracle on sampled pixels over every frame
+    (velocity and the whitened output against the oracle's own)."""
+    T = 8
+    sc = scenes.small_scene(T=T, H=H, W=W, seed=31, vx=0.8, vy=-0.6, tex_size=512)
+    g = P.run_gpu(sc.frames, 15, 6, 3.0, 0.25, debug=False)
+    o = oracle.Oracle(15, 6, 3.0, 0.25)
+    rng = np.random.default_rng(5)
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (H // 2, W // 2)]
+    pts += [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(11)]
+    same, n, wmax = 0, 0, 0.0
+    for (y, x) in pts:
+        ref = o.run(sc.frames, crop=(y, x, 1, 1))
+        gi = g["vel_index"][:, y:y + 1, x:x + 1]
+        ri = ref["vel_index"]
+        same += int(np.sum(gi[1:] == ri[1:]))
+        n += T - 1
+        d = np.maximum(np.abs(gi % o.L - ri % o.L), np.abs(gi // o.L - ri // o.L))
+        assert np.all(d[1:] <= 1), (y, x, d.ravel())
+        wr = P.whitened_report(g["whitened"][:, y:y + 1, x:x + 1], gi, ref["whitened"], ri, sc.frames, o.mpz)
+        assert wr["matched"] <= P.WHITE_TOL_REL, (y, x, wr)
+        wmax = max(wmax, wr["matched"])
+    print(f"\n[parity {H}x{W} sampled] velocity identical {same}/{n}, whitened vs oracle {wmax:.2e} xRMS",
+          flush=True)
+    assert same >= n - 1
+
+
+def test_parity_single_velocity_grid():
+    """A grid of one point (vmax = 0, L = 1): the search returns it everywhere
+    and the filter is the one tuned to v = 0."""
+    sc = scenes.small_scene(T=10, H=30, W=44, seed=9, vx=0.2, vy=0.1, tex_size=128)
+    g = P.run_gpu(sc.frames, 9, 4, 0.0, 0.25, debug=False)
+    assert np.all(g["vel_index"] == 0)
+    o = oracle.Oracle(9, 4, 0.0, 0.25)
+    assert o.L == 1
+    ref = o.run(sc.frames)
+    assert P.whitened_err(g["whitened"], ref["whitened"], sc.frames, o.mpz) <= P.WHITE_TOL_REL
