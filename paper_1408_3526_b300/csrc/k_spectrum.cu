@@ -169,7 +169,7 @@ struct SG {
   static constexpr int NBINS = M * M * MZ;
   static constexpr size_t O_FGS = al16(O_OFFS + 8ull * NPL);                   // int   [NBINS] gather
   static constexpr size_t O_FPART = al16(O_FGS + 4ull * NBINS);                // float [TW][NH1]
-  static constexpr size_t O_FTOT = al16(O_FPART + 4ull * TW * NH1);            // float [TW]
+  static constexpr size_t O_FTOT = al16(O_FPART + 4ull * TW * NH1);            // float [TW] 1/sum P
   static constexpr size_t SMEM = al16(O_FTOT + 4ull * TW);
   static_assert(RW <= 32, "the observer warp covers the row segment");
   static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
@@ -682,7 +682,10 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the bulk store
       // learned-estimator features of this output row, (log2(P / sum P + 1e-6) + 10) / 10
-      // of every bin in [kz][ky][kx] order, BF16, written 8 bins per 16-byte store
+      // of every requested bin, BF16.  Lanes take consecutive bin pairs (one
+      // 4-byte store each, 128 contiguous bytes per warp; gathers from the power
+      // block at most 2-way bank-conflicted), and a thread's two gather offsets
+      // serve all TW pixels of the row.
       if (feat) {
         constexpr int NDW = NTW / 32;
         asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");   // all partial sums of the row
@@ -691,28 +694,23 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
           for (int h = lane; h < NH1; h += 32) t += fpart[x * NH1 + h];
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-          if (lane == 0) ftot[x] = t;
+          if (lane == 0) ftot[x] = t > 0.f ? 1.f / t : 0.f;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");
-        const int nv = a.feat_ld / 8, nfeat = a.feat_n;
-        for (int task = tid; task < TW * nv; task += NTW) {
-          const int x = task / nv, v = task - x * nv;
-          if (x0 + x >= W) continue;
-          const float tot = ftot[x];
-          const float inv = tot > 0.f ? 1.f / tot : 0.f;
-          const float* pb = pbuf + x * PS;
-          uint32_t packed[4];
+        const int np = a.feat_ld / 2, nfeat = a.feat_n;
+        __nv_bfloat162* frow = reinterpret_cast<__nv_bfloat162*>(a.feat) + (size_t(yo) * W + x0) * np;
+        for (int j = tid; j < np; j += NTW) {
+          const int b0 = 2 * j;
+          const int g0 = b0 < nfeat ? fgs[b0] : -1, g1 = b0 + 1 < nfeat ? fgs[b0 + 1] : -1;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int b0 = 8 * v + 2 * q;
-            const float f0 = b0 < nfeat ? 0.1f * (__log2f(fmaf(pb[fgs[b0]], inv, 1e-6f)) + 10.f) : 0.f;
-            const float f1 = b0 + 1 < nfeat ? 0.1f * (__log2f(fmaf(pb[fgs[b0 + 1]], inv, 1e-6f)) + 10.f) : 0.f;
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(f0, f1);
-            packed[q] = *reinterpret_cast<const uint32_t*>(&h2);
+          for (int x = 0; x < TW; ++x) {
+            if (x0 + x >= W) break;
+            const float inv = ftot[x];
+            const float* pb = pbuf + x * PS;
+            const float f0 = g0 >= 0 ? 0.1f * (__log2f(fmaf(pb[g0], inv, 1e-6f)) + 10.f) : 0.f;
+            const float f1 = g1 >= 0 ? 0.1f * (__log2f(fmaf(pb[g1], inv, 1e-6f)) + 10.f) : 0.f;
+            frow[size_t(x) * np + j] = __floats2bfloat162_rn(f0, f1);
           }
-          uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.feat) +
-                                                (size_t(yo) * W + x0 + x) * a.feat_ld) + v;
-          *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
       }
     };
