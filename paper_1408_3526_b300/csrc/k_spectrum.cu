@@ -337,6 +337,16 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
   const int dbase = bown ? NOB * RD + tid : tid - NBT;
   const int dstride = bown ? NBT : NOB;
   const bool dthr = tid < NTW;
+  // this thread's reduction tasks, fixed for the whole kernel: column x in the
+  // low byte (0xff: no task), h above it
+  constexpr int RQ = RB > RD ? RB : RD;
+  uint32_t dtask[RQ];
+#pragma unroll
+  for (int q = 0; q < RQ; ++q) {
+    const int d = dbase + q * dstride;
+    const bool ok = dthr && q < (bown ? RB : RD) && d < NDT;
+    dtask[q] = ok ? uint32_t(d / NH1) | (uint32_t(d % NH1) << 8) : 0xffu;
+  }
 
   // ---- this CTA's share of the (strip, row) units -------------------------------
   // Units (strip, output row) in strip-major order; every segment a CTA walks
@@ -646,9 +656,9 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       const int b = row_slot(r);
       if (!tc::mbar_wait(&mbar[b], uint32_t(((gbase + r) / 3) & 1), 1000000000ull)) timed_out = true;
       float* st = srow + b * G::SROW;
-      auto one = [&](int d) {
-        const int x = d / NH1, hi = d - x * NH1;
-        if (d >= NDT || x0 + x >= W) return;
+      auto one = [&](uint32_t t) {
+        const int x = int(t & 0xffu), hi = int(t >> 8);
+        if (x >= ncols) return;
         // P(h, kz) for the slots kz = 0, +j, -j (= P(-h, +j)), Mz/2 of this h:
         // offsets x*PS + (c*M + ky + K) with c the channel of (plane, +-hx)
         const int op = x * PS + hi + K, om = x * PS - hi + K;
@@ -675,10 +685,10 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       };
       if (bown) {
 #pragma unroll
-        for (int q = 0; q < RB; ++q) one(dbase + q * dstride);
+        for (int q = 0; q < RB; ++q) one(dtask[q]);
       } else {
 #pragma unroll
-        for (int q = 0; q < RD; ++q) one(dbase + q * dstride);
+        for (int q = 0; q < RD; ++q) one(dtask[q]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the bulk store
       // learned-estimator features of this output row, (log2(P / sum P + 1e-6) + 10) / 10

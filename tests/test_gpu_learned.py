@@ -9,6 +9,7 @@ import oracle
 from oracle import mlp as omlp
 from paper_1408_3526_b300 import scenes
 from tests import _mlp_bounds as B
+from tests import _parity as P
 
 pytestmark = pytest.mark.gpu
 
@@ -154,12 +155,21 @@ def test_training_gains_and_learned_mode():
     frames, _ = next(scenes.training_scene_set(1, T, H, W, seed0=777))
     fd = torch.from_numpy(frames).cuda()
     res = {}
+    seq = {}
     for name, net in [("plain", None), ("trained", trained), ("untrained", untrained)]:
         with WhitenStream(H, W, M, Mz, vmax, step) as s:
             if net is not None:
                 assert s.lib.wh_stream_set_learned(s._s, net._m, 0.8) == 0
+            vel_seq = np.zeros((T, H, W), np.int32)
+            wh_seq = np.full((T, H, W), np.nan)
             for t in range(T):
                 s.push(fd[t])
+                _, _, vi_t, ti = s.read_velocity()
+                assert ti == t
+                vel_seq[t] = vi_t
+                if t >= s.delay_z:
+                    wh_seq[t], _ = s.read_whitened()
+            seq[name] = (vel_seq, wh_seq, s.delay_z)
             _, _, vi, _ = s.read_velocity()
             fr, fb = C.c_longlong(), C.c_longlong()
             s.lib.wh_stream_learned_stats(s._s, C.byref(fr), C.byref(fb))
@@ -177,5 +187,20 @@ def test_training_gains_and_learned_mode():
     assert res["trained"][2] >= 0.95
     acc_t, acc_u = 1 - res["trained"][1], 1 - res["untrained"][1]
     assert acc_t >= 0.5 and acc_t > acc_u + 0.3
+    # against the FP64 oracle on a 24 x 24 crop: the learned velocities sit
+    # within one grid step of the oracle's own argmax, and the whitened output
+    # is the oracle's filter on the learned velocity field
+    vel_l, wh_l, dz = seq["trained"]
+    y0, x0, h, w = 36, 36, 24, 24
+    o = oracle.Oracle(M, Mz, vmax, step)
+    ref = o.run(frames, crop=(y0, x0, h, w))
+    vl = vel_l[:, y0:y0 + h, x0:x0 + w]
+    d = np.maximum(np.abs(vl[-1] % L - ref["vel_index"][-1] % L), np.abs(vl[-1] // L - ref["vel_index"][-1] // L))
+    ref_l = o.run(frames, crop=(y0, x0, h, w), vel_override=vl)
+    werr = P.whitened_err(wh_l[:, y0:y0 + h, x0:x0 + w], ref_l["whitened"], frames, dz)
+    print(f"[learned vs oracle] within one step {np.mean(d <= 1):.3f}, whitened on the learned field "
+          f"{werr:.2e} x input RMS", flush=True)
+    assert np.mean(d <= 1) >= 0.95
+    assert werr <= P.WHITE_TOL_REL
     trained.close()
     untrained.close()
