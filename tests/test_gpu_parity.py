@@ -169,6 +169,35 @@ def test_parity_full_size_config2_sampled():
     assert same >= P.VEL_EXACT_FRAC * n
 
 
+def test_parity_full_frames_config2_first12():
+    """512 x 640, 15 x 15, order 6, grid +-3/0.25: every pixel of the first 12
+    frames against the oracle run on the whole frame (its own velocities, no
+    conditioning): smoothed R' of the last frame, velocity
+    indices identical except at the oracle's near-ties (one grid step at most
+    there), whitened output at every pixel-frame whose velocity agrees."""
+    T = 12
+    sc = scenes.config2_scene(T=T)
+    g = P.run_gpu(sc.frames, 15, 6, 3.0, 0.25, spec_frames=(T - 1,), debug=False)
+    o = oracle.Oracle(15, 6, 3.0, 0.25)
+    ref = o.run(sc.frames, spec_frames=[T - 1], autocorr=True)
+    ar = ref["autocorr"][0]
+    scale = np.abs(ar).reshape(512, 640, -1).max(-1)[..., None, None]
+    rs_err = float(np.max(np.abs(g["autocorr"][T - 1] - ar) / np.maximum(scale, 1e-30)))
+    frac, steps, tie, bad = P.velocity_report(g["vel_index"], ref["vel_index"], {T - 1: ar}, o.L)
+    wr = P.whitened_report(g["whitened"], g["vel_index"], ref["whitened"], ref["vel_index"], sc.frames,
+                           o.mpz)
+    print(f"\n[parity 512x640 full, 12 frames] R' {rs_err:.2e} vel_same {frac:.5f} max_steps {steps} "
+          f"tie {tie:.2e} whitened vs oracle {wr['matched']:.2e} xRMS ({wr['matched_clutter']:.2e} x clutter "
+          f"RMS), near-tie pixel-frames {wr['mismatched_frac']:.1e}: {wr['mismatched']:.2e} xRMS; "
+          f"mismatches {bad[:6]}", flush=True)
+    assert rs_err <= P.SPEC_TOL
+    assert frac >= P.VEL_EXACT_FRAC, (frac, bad)
+    assert steps <= 1, (steps, bad)
+    assert tie <= P.TIE_TOL, (tie, bad)
+    assert wr["matched"] <= P.WHITE_TOL_REL, wr
+    assert wr["matched_clutter"] <= P.WHITE_TOL_CLUTTER, wr
+
+
 @pytest.mark.parametrize("H,W", [(4096, 4096), (8, 65536), (65536, 8)],
                          ids=["4096x4096", "8x65536", "65536x8"])
 def test_parity_large_and_extreme_shapes(H, W):
