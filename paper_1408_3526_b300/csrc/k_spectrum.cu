@@ -712,13 +712,20 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         for (int j = tid; j < np; j += NTW) {
           const int b0 = 2 * j;
           const int g0 = b0 < nfeat ? fgs[b0] : -1, g1 = b0 + 1 < nfeat ? fgs[b0 + 1] : -1;
+          // every shared-memory read of the TW pixels first: the global stores
+          // would otherwise order the next pixel's reads behind them
+          float v0[TW], v1[TW], iv[TW];
+#pragma unroll
+          for (int x = 0; x < TW; ++x) {
+            iv[x] = ftot[x];
+            v0[x] = pbuf[x * PS + (g0 >= 0 ? g0 : 0)];
+            v1[x] = pbuf[x * PS + (g1 >= 0 ? g1 : 0)];
+          }
 #pragma unroll
           for (int x = 0; x < TW; ++x) {
             if (x0 + x >= W) break;
-            const float inv = ftot[x];
-            const float* pb = pbuf + x * PS;
-            const float f0 = g0 >= 0 ? 0.1f * (__log2f(fmaf(pb[g0], inv, 1e-6f)) + 10.f) : 0.f;
-            const float f1 = g1 >= 0 ? 0.1f * (__log2f(fmaf(pb[g1], inv, 1e-6f)) + 10.f) : 0.f;
+            const float f0 = g0 >= 0 ? 0.1f * (__log2f(fmaf(v0[x], iv[x], 1e-6f)) + 10.f) : 0.f;
+            const float f1 = g1 >= 0 ? 0.1f * (__log2f(fmaf(v1[x], iv[x], 1e-6f)) + 10.f) : 0.f;
             frow[size_t(x) * np + j] = __floats2bfloat162_rn(f0, f1);
           }
         }
