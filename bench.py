@@ -59,6 +59,9 @@ PROFILE_OF = {
     "autocorr_argmax": ("profiles/autocorr_512x640_m15.md", ["k_autocorr.cu", "ac_common.cuh", "common.cuh"]),
     "pef": ("profiles/pef_512x640_m15_mz6.md", ["k_pef.cu", "common.cuh"]),
 }
+# the search kernel's summary for the whole-contraction tensor-core engine (--precision 128)
+PROFILE_OF_TCD = ("profiles/autocorr_tcd_512x640_m15.md",
+                  ["k_autocorr_tcd.cu", "ac_common.cuh", "common.cuh", "tc_ptx.cuh"])
 # the search kernel's summary when the tensor-core separable engine runs (--precision 32)
 PROFILE_OF_TCSEP = ("profiles/autocorr_tcsep_512x640_m15.md",
                     ["k_autocorr_tcsep.cu", "ac_common.cuh", "common.cuh", "tc_ptx.cuh"])
@@ -130,6 +133,9 @@ def engine_name(precision):
         name = "tensor-core contraction alone (%s)" % ("BF16" if precision & 2 else "F16")
     elif precision & 32:
         name = "FP32-exact separable search, first stage on tensor cores (TF32 row bounds)"
+    elif precision & 128:
+        name = ("FP32-exact argmax: whole contraction on tcgen05 tensor cores (F16, F32 accumulation) "
+                "with a rigorous error window, near ties re-evaluated in FP32")
     else:
         name = "FP32-exact separable search on CUDA cores"
     if precision & 64:
@@ -301,14 +307,18 @@ def main():
     ap.add_argument("--no-pipeline", action="store_true",
                     help="serial stream (no overlap of consecutive frames)")
     ap.add_argument("--precision", type=int, default=0,
-                    help="wh_params.precision (0: FP32-exact search on CUDA cores; 16: tensor-core "
-                         "shortlist + exact re-rank)")
+                    help="wh_params.precision (0: FP32-exact separable search on CUDA cores; 16: "
+                         "tensor-core shortlist + exact re-rank; 32: separable search with its first "
+                         "stage on tensor cores; 128: FP32-exact argmax with the whole contraction on "
+                         "tensor cores)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
     if (args.precision & 32) and not (args.precision & (16 | 3)):
         PROFILE_OF["autocorr_argmax"] = PROFILE_OF_TCSEP
+    elif (args.precision & 128) and not (args.precision & (8 | 16 | 32 | 3)):
+        PROFILE_OF["autocorr_argmax"] = PROFILE_OF_TCD
 
     import torch
     import torch.distributed as dist

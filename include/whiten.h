@@ -67,6 +67,16 @@ extern "C" {
  *   bound reaches the best row's exact value are evaluated in FP32 on CUDA
  *   cores, so the velocity is identical to the CUDA-core search's.  Windows
  *   5..15, grids up to 31 x 31.
+ * WH_PREC_TC_DENSE: the exact FP32 argmax with the whole contraction of
+ *   Eq. (10) on tcgen05 tensor cores: per pixel the state is scaled by a power
+ *   of two and rounded to F16, C(l) and S(l) (R(l) = C + S, R(-l) = C - S) come
+ *   from one F16 product with F32 accumulation over the half grid, and a grid
+ *   point is decided by the tensor cores alone when it is the only one within
+ *   the rigorous error window of the maximum; otherwise the (at most 8) points
+ *   within it, or the whole grid, are evaluated exactly in FP32 with the
+ *   CUDA-core search's operation sequence, so the velocity is identical to that
+ *   search's.  Windows 5..15, grids up to 31 x 31; wh_stream_search_counts
+ *   reports how many pixel-frames needed the exact evaluation.
  * WH_PREC_CUDA_CORES: the separable evaluation on CUDA cores only.
  * WH_PREC_SPEC_F64 (combinable with the search flags): the precision form of the
  *   recursive spectrum: the spatial sums (x-direction DFT, comb differences and
@@ -83,6 +93,7 @@ extern "C" {
 #define WH_PREC_TC_SHORTLIST 16
 #define WH_PREC_TC_SEPARABLE 32
 #define WH_PREC_SPEC_F64     64
+#define WH_PREC_TC_DENSE    128
 
 /* Velocity grid: {-vmax, -vmax + step, ..., +vmax} on both axes
  * (Sec. 3: l_x = l_y = [-8 .. 8]/4, a 17 x 17 grid at vmax = 2, step 1/4).
@@ -350,6 +361,15 @@ int wh_stream_info(const wh_stream *s, int *grid_len, int *delay_z, int *band,
 /* Counters: pixel-frames whose tensor-core shortlist could be incomplete and
  * were evaluated on the whole grid (WH_PREC_TC_SHORTLIST only; else 0). */
 int wh_stream_stats(wh_stream *s, long long *fallback_pixels);
+
+/* Counters of the default search engine (the whole contraction of Eq. (10)
+ * on tensor cores; zero for the other engines), accumulated since the stream
+ * was created: pixel-frames whose F16 tensor-core values left 2..8 grid
+ * points within the rigorous error window of the maximum (those points were
+ * evaluated exactly in FP32), and pixel-frames evaluated exactly on the whole
+ * grid (more points, or a non-finite or subnormal-range state).  Every other
+ * pixel-frame was decided by the tensor-core product alone. */
+int wh_stream_search_counts(wh_stream *s, long long *listed_pixels, long long *whole_grid_pixels);
 
 /* Device pointers of the stream's output buffers (valid until destroy):
  * whitened[h][w], vx[h][w], vy[h][w] (float32), vidx[h][w] (int32).

@@ -29,6 +29,7 @@ WH_PREC_CUDA_CORES = 8
 WH_PREC_TC_SHORTLIST = 16
 WH_PREC_TC_SEPARABLE = 32
 WH_PREC_SPEC_F64 = 64
+WH_PREC_TC_DENSE = 128
 
 WH_SPEC_RAW = 0
 WH_SPEC_WINDOWED = 1
@@ -78,6 +79,7 @@ _SIGS = {
     "wh_stream_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong)]),
     "wh_stream_stats": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+    "wh_stream_search_counts": (C.c_int, [_VP, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "wh_tcsep_operand": (C.c_int, [C.c_int, C.c_int, C.c_double, _VP]),
     "wh_output_pointers": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
                                      C.POINTER(_VP)]),

@@ -120,6 +120,25 @@ struct TcSepArgs {
   int* err;
 };
 
+// Autocorrelation search with the whole contraction on tensor cores
+// (k_autocorr_tcd.cu): per pixel the F16 product decides alone where one grid
+// point lies within the rigorous error window of the maximum; the others are
+// listed (ccount > 0 points in cand, or -1: the whole grid) and evaluated
+// exactly in FP32 by the same kernel.
+struct TcDenseArgs {
+  int npix, M, L, kpad;
+  float vmax, vstep;
+  const float* Astate;
+  int* vidx;
+  float* vx;
+  float* vy;
+  const float2* tab_x;          // e^{j2pi kx lx/M}: [L][K+1]
+  int* ccount;                  // [npix] scratch
+  int* cand;                    // [npix][8] scratch
+  unsigned long long* counts;   // optional: [0] pixels with listed points, [1] whole-grid pixels
+  int* err;
+};
+
 struct PefArgs {
   int H, W, M, Mz, L, mpz;
   const float* obs;             // T_t, just written
@@ -199,6 +218,12 @@ cudaError_t launch_autocorr_convert(const AutocorrTcArgs& a, cudaStream_t st);
 cudaError_t launch_autocorr_rerank(const AutocorrTcArgs& a, cudaStream_t st);
 bool autocorr_tcsep_supported(int M, int L);
 cudaError_t launch_autocorr_tcsep(const TcSepArgs& a, cudaStream_t st);
+bool autocorr_tcd_supported(int M, int L);
+// table: the constant F16 operand, tcd_table_rows(L) rows of tcd_table_ld(M) values
+cudaError_t launch_autocorr_tcd(const TcDenseArgs& a, const void* table, cudaStream_t st);
+int tcd_table_rows(int L);
+int tcd_table_ld(int M);
+void build_tcd_table(int M, int L, double vmax, double vstep, uint16_t* out);
 // Stage-1 operand of the tensor-core separable search (2048 floats, see TcSepArgs)
 void build_tcsep_operand(int M, int L, double vstep, float* out);
 

@@ -214,6 +214,13 @@ long long wh_stream_device_bytes_opt(int h, int w, int window, int temporal_orde
   const long long L = (long long)(2.0 * grid.vmax / grid.step + 1.5);
   // observer ping-pong, smoothed state, frame, whitened/vx/vy/vidx, tables
   long long b = npix * (2LL * temporal_order * 4 + kpad * 4 + 4 + 16) + L * 64 * 1024 + (1 << 20);
+  const int prec0 = opt ? opt->precision : 0;
+  if ((prec0 & 3) == 0 && (prec0 & WH_PREC_TC_DENSE) &&
+      !(prec0 & (WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST | WH_PREC_TC_SEPARABLE))) {
+    // whole contraction on tensor cores: per-pixel listed points and the operand
+    const long long nhg = (L * L + 1) / 2, nch = (nhg + 127) / 128;
+    b += npix * 4 * 9 + 2 * nch * 128 * 128 * 2;
+  }
   if (opt) {
     if (opt->pipeline) b += npix * kpad * 4;                       // second smoothed-state buffer
     const int prec = opt->precision;

@@ -230,7 +230,8 @@ static void free_stream(wh_stream* s) {
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
                   s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
                   s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather, s->d_ymlp,
-                  s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list, s->d_bop};
+                  s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list, s->d_bop,
+                  s->d_tcd_table, s->d_ccount, s->d_cand, s->d_tcd_counts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -278,7 +279,8 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   if (p.band > K || p.delay_z >= Mz || p.alpha >= 1.0) return WH_EINVAL;
   if (!spectrum_supported(M, Mz)) return WH_EUNSUP;
   const int pmode = p.precision & 3;
-  if (p.precision & ~(3 | WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST | WH_PREC_TC_SEPARABLE | WH_PREC_SPEC_F64))
+  if (p.precision &
+      ~(3 | WH_PREC_CUDA_CORES | WH_PREC_TC_SHORTLIST | WH_PREC_TC_SEPARABLE | WH_PREC_SPEC_F64 | WH_PREC_TC_DENSE))
     return WH_EUNSUP;
   if (pmode == 3) return WH_EINVAL;
   if (pmode != 0 && !autocorr_tc_supported(M)) return WH_EUNSUP;
@@ -299,7 +301,11 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->as = nullptr;
   s->d_det = nullptr; s->det_bytes = 0; s->d_det_list = nullptr; s->det_list_cap = 0;
   s->d_bop = nullptr;
+  s->d_tcd_table = nullptr; s->d_ccount = nullptr; s->d_cand = nullptr; s->d_tcd_counts = nullptr;
   s->spec_f64 = (p.precision & WH_PREC_SPEC_F64) ? 1 : 0;
+  s->use_tcd = pmode == 0 && (p.precision & WH_PREC_TC_DENSE) &&
+               !(p.precision & (WH_PREC_TC_SHORTLIST | WH_PREC_CUDA_CORES | WH_PREC_TC_SEPARABLE)) &&
+               autocorr_tcd_supported(M, L);
   s->use_tcsep = pmode == 0 && !(p.precision & (WH_PREC_TC_SHORTLIST | WH_PREC_CUDA_CORES)) &&
                  (p.precision & WH_PREC_TC_SEPARABLE) && autocorr_tcsep_supported(M, L);
   s->tc_mode = pmode == 0 ? 0 : 1;
@@ -408,6 +414,22 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
       free_stream(s);
       return rc;
     }
+  if (s->use_tcd) {
+    const size_t nt = size_t(tcd_table_rows(L)) * tcd_table_ld(M);
+    std::vector<uint16_t> tab(nt);
+    build_tcd_table(M, L, s->vmax, s->vstep, tab.data());
+    alloc((void**)&s->d_tcd_table, sizeof(uint16_t) * nt);
+    alloc((void**)&s->d_ccount, sizeof(int) * npix);
+    alloc((void**)&s->d_cand, sizeof(int) * 8 * npix);
+    alloc((void**)&s->d_tcd_counts, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_tcd_table, tab.data(), sizeof(uint16_t) * nt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->d_tcd_counts, 0, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      int rc = (e == cudaErrorMemoryAllocation) ? WH_ENOMEM : set_cuda_err(e, "tensor-core search operand");
+      free_stream(s);
+      return rc;
+    }
+  }
   if (s->use_tcsep) {
     std::vector<float> bop(2048);
     build_tcsep_operand(M, L, s->vstep, bop.data());
@@ -602,6 +624,15 @@ static int push_kernels(wh_stream* s, const float* src, cudaEvent_t wait_spec = 
     if (rc == WH_OK && (e = launch_autocorr_rerank(ta, sp)) != cudaSuccess)
       rc = set_cuda_err(e, "autocorrelation re-rank kernel");
     nlaunch = 5;
+  } else if (s->use_tcd) {
+    TcDenseArgs ta{};
+    ta.npix = s->H * s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad;
+    ta.vmax = float(s->vmax); ta.vstep = float(s->vstep);
+    ta.Astate = s->Astate; ta.vidx = s->vidx; ta.vx = s->vx; ta.vy = s->vy;
+    ta.tab_x = s->d_tabx; ta.ccount = s->d_ccount; ta.cand = s->d_cand; ta.counts = s->d_tcd_counts;
+    ta.err = s->d_err;
+    if ((e = launch_autocorr_tcd(ta, s->d_tcd_table, sp)) != cudaSuccess)
+      rc = set_cuda_err(e, "tensor-core search kernel");
   } else if (s->use_tcsep) {
     TcSepArgs ta{};
     ta.npix = s->H * s->W; ta.M = s->M; ta.L = s->L; ta.kpad = s->kpad;
@@ -874,6 +905,17 @@ int wh_stream_stats(wh_stream* s, long long* fallback_pixels) {
   WH_CU(cudaStreamSynchronize(s->st));
   if (s->d_nfb) WH_CU(cudaMemcpy(&h, s->d_nfb, sizeof(int), cudaMemcpyDeviceToHost));
   if (fallback_pixels) *fallback_pixels = h;
+  return check_device_status(s);
+}
+
+int wh_stream_search_counts(wh_stream* s, long long* listed_pixels, long long* whole_grid_pixels) {
+  if (!s) return WH_EINVAL;
+  { const int jr = join_pipeline(s); if (jr != WH_OK) return jr; }
+  unsigned long long h[2] = {0ull, 0ull};
+  WH_CU(cudaStreamSynchronize(s->st));
+  if (s->d_tcd_counts) WH_CU(cudaMemcpy(h, s->d_tcd_counts, sizeof(h), cudaMemcpyDeviceToHost));
+  if (listed_pixels) *listed_pixels = (long long)h[0];
+  if (whole_grid_pixels) *whole_grid_pixels = (long long)h[1];
   return check_device_status(s);
 }
 

@@ -41,6 +41,12 @@ struct wh_stream {
   void* d_table;
   int* d_err;
   int* d_nfb;
+  // autocorrelation search with the whole contraction on tensor cores (default)
+  int use_tcd;
+  void* d_tcd_table;     // constant F16 operand
+  int* d_ccount;         // [H*W] per-pixel code of listed grid points
+  int* d_cand;           // [H*W][8] listed grid points
+  unsigned long long* d_tcd_counts;   // [2] pixel-frames with listed points / whole grid
   // autocorrelation search with the separable stage on tensor cores
   int use_tcsep;
   int spec_f64;          // the precision form of the spectrum kernel (spatial sums in double)

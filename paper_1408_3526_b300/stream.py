@@ -212,6 +212,13 @@ class WhitenStream:
         check(self.lib.wh_profile_read(self._s, ms, n, int(bool(reset))), "wh_profile_read")
         return list(ms), int(n[0])
 
+    def search_counts(self):
+        """(listed, whole_grid) pixel-frames of the default tensor-core search
+        since creation (wh_stream_search_counts)."""
+        a, b = C.c_longlong(), C.c_longlong()
+        check(self.lib.wh_stream_search_counts(self._s, C.byref(a), C.byref(b)), "wh_stream_search_counts")
+        return int(a.value), int(b.value)
+
     def grid_values(self) -> np.ndarray:
         return -self.vmax + self.step * np.arange(self.L)
 

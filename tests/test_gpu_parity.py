@@ -75,8 +75,9 @@ def test_parity_paper_simulation_precision_form():
     _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), precision=64)
 
 
-@pytest.mark.parametrize("precision", [16, 0, 32, 64 | 32],
-                         ids=["tc_shortlist_rerank", "cuda_cores", "tc_separable", "f64_sums_tc_separable"])
+@pytest.mark.parametrize("precision", [16, 0, 128, 32, 64 | 32],
+                         ids=["tc_shortlist_rerank", "cuda_cores", "tc_dense", "tc_separable",
+                              "f64_sums_tc_separable"])
 def test_parity_config1_full(precision):
     """64 x 64 x 32 frames, 9 x 9 window, order 4, grid +-2 step 1/4 (in full),
     with both FP32-exact engines of the autocorrelation search."""
@@ -84,7 +85,8 @@ def test_parity_config1_full(precision):
     _compare(sc.frames, 9, 4, 2.0, 0.25, spec_frames=(3, 31), precision=precision)
 
 
-@pytest.mark.parametrize("precision", [16, 0, 32], ids=["tc_shortlist_rerank", "cuda_cores", "tc_separable"])
+@pytest.mark.parametrize("precision", [16, 0, 128, 32],
+                         ids=["tc_shortlist_rerank", "cuda_cores", "tc_dense", "tc_separable"])
 def test_parity_config2_shape_crop(precision):
     """15 x 15 window, order 6, grid +-3 step 1/4 on a 40 x 56 crop of the
     non-uniform-flow scene (several tiles, ragged tail)."""

@@ -39,7 +39,8 @@ def _cases(n=10, seed=2024):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 16, 32], ids=["cuda_cores", "tc_shortlist_rerank", "tc_separable"])
+@pytest.mark.parametrize("precision", [0, 128, 16, 32],
+                         ids=["cuda_cores", "tc_dense", "tc_shortlist_rerank", "tc_separable"])
 @pytest.mark.parametrize("i,M,Mz,vmax,step,H,W,vx,vy", _cases(),
                          ids=lambda v: str(v) if isinstance(v, int) else None)
 def test_parity_random_shape(i, M, Mz, vmax, step, H, W, vx, vy, precision):

@@ -46,7 +46,7 @@ def _same(a, b):
             assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("precision", [0, 16], ids=["cuda_cores", "tc_shortlist_rerank"])
+@pytest.mark.parametrize("precision", [0, 128, 16], ids=["cuda_cores", "tc_dense", "tc_shortlist_rerank"])
 def test_pipeline_identical_to_serial(precision):
     fr = scenes.config1_scene(T=T, H=H, W=W, seed=9).frames.astype(np.float32)
     _same(_run(fr, False, precision), _run(fr, True, precision))

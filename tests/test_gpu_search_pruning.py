@@ -56,7 +56,7 @@ def _lowest_argmax(R):
     return np.argmax(flat, axis=-1)      # numpy returns the first occurrence
 
 
-@pytest.mark.parametrize("precision", [0, 32], ids=["cuda_cores", "tc_separable"])
+@pytest.mark.parametrize("precision", [0, 128, 32], ids=["cuda_cores", "tc_dense", "tc_separable"])
 @pytest.mark.parametrize("kind", ["flow", "paper_sim", "noise", "constant", "impulse", "nan"])
 @pytest.mark.parametrize("M,Mz,vmax,step", [(15, 6, 3.0, 0.25), (9, 4, 2.0, 0.25), (7, 5, 3.75, 0.25),
                                              (15, 6, 3.75, 0.25)])
