@@ -304,6 +304,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--profile-steps", type=int, default=20,
                     help="frames of the serial pass that times each kernel alone (roofline)")
+    ap.add_argument("--no-tc-engine", action="store_true",
+                    help="skip the secondary measurement of the whole-contraction tensor-core search "
+                         "(--precision 128) on the same workload")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="serial stream (no overlap of consecutive frames)")
     ap.add_argument("--precision", type=int, default=0,
@@ -376,6 +379,49 @@ def main():
         kms, nprof = sk.profile_read(reset=True)
     value = whole_job_mpx_per_s(world, args.steps, ms_max * 1e-3)
 
+    # the same step with the whole contraction of Eq. (10) on tcgen05 tensor cores
+    # (exact, identical velocities; slower than the default CUDA-core search)
+    tc_engine = None
+    if not args.no_tc_engine and args.precision == 0:
+        nt = min(args.steps, 50)
+        with WhitenStream(H, W, M, MZ, VMAX, VSTEP, cuda_stream=stream, precision=128,
+                          pipeline=pipeline) as st:
+            with torch.cuda.stream(stream):
+                for i in range(args.warmup):
+                    st.push(frames_d[i % NFRAMES_RESIDENT])
+            st.join()
+            torch.cuda.synchronize()
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for i in range(nt):
+                st.push(frames_d[(args.warmup + i) % NFRAMES_RESIDENT])
+            st.join()
+            f1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            tms = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
+            listed, whole = st.search_counts()
+        with WhitenStream(H, W, M, MZ, VMAX, VSTEP, cuda_stream=stream, precision=128) as sk:
+            with torch.cuda.stream(stream):
+                for i in range(3):
+                    sk.push(frames_d[i % NFRAMES_RESIDENT])
+            torch.cuda.synchronize()
+            sk.profile(True)
+            sk.profile_read(reset=True)
+            with torch.cuda.stream(stream):
+                for i in range(args.profile_steps):
+                    sk.push(frames_d[(3 + i) % NFRAMES_RESIDENT])
+            torch.cuda.synchronize()
+            tkms, tn = sk.profile_read(reset=True)
+        frames_seen = args.warmup + nt
+        tc_engine = {"engine": engine_name(128), "precision": 128,
+                     "value": round(whole_job_mpx_per_s(world, nt, tms * 1e-3), 3), "unit": "Mpixel/s",
+                     "steps": nt, "ms_per_step": round(tms / nt, 5),
+                     "search_ms": round(tkms[1] / max(tn, 1), 5),
+                     "pixel_frames_exact_step": round((listed + whole) / (frames_seen * H * W), 4),
+                     "profile": PROFILE_OF_TCD[0]}
+
     # end to end through the C ABI: pinned host frame in, whitened + velocity out
     pin_in = torch.from_numpy(frames_h[:8].copy()).pin_memory()
     out_w = torch.empty((H, W), dtype=torch.float32).pin_memory()
@@ -406,7 +452,8 @@ def main():
     # end-to-end pass (the same kernels back to back), so a short timed region
     # still gets a clock record under the same load
     clk = clocks.stop()
-    clk["window"] = "timed region + per-kernel serial pass + end-to-end pass"
+    clk["window"] = ("timed region + per-kernel serial pass + tensor-core search pass + end-to-end pass"
+                     if tc_engine is not None else "timed region + per-kernel serial pass + end-to-end pass")
 
     if rank == 0:
         hbm, src = peaks()
@@ -445,6 +492,8 @@ def main():
             "clocks": clk,
         }
         line["config"]["engine"] = engine_name(args.precision)
+        if tc_engine is not None:
+            line["tensor_core_search"] = tc_engine
         if args.precision & 16:
             import ctypes as C
             fb = C.c_longlong()

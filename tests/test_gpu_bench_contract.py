@@ -35,5 +35,8 @@ def test_bench_line_has_the_contract_fields():
     assert e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] >= 3 * d["steps"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+    tc = d["tensor_core_search"]            # the tcgen05 engine measured on the same workload
+    assert tc["precision"] == 128 and tc["value"] > 0 and tc["search_ms"] > 0
+    assert 0 <= tc["pixel_frames_exact_step"] < 1
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
