@@ -708,25 +708,44 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         }
         asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");
         const int np = a.feat_ld / 2, nfeat = a.feat_n;
+        const int nx = W - x0 < TW ? W - x0 : TW;
         __nv_bfloat162* frow = reinterpret_cast<__nv_bfloat162*>(a.feat) + (size_t(yo) * W + x0) * np;
+        float2 iv2[TW];
+#pragma unroll
+        for (int x = 0; x < TW; ++x) iv2[x] = make_float2(ftot[x], ftot[x]);
         for (int j = tid; j < np; j += NTW) {
           const int b0 = 2 * j;
-          const int g0 = b0 < nfeat ? fgs[b0] : -1, g1 = b0 + 1 < nfeat ? fgs[b0 + 1] : -1;
-          // every shared-memory read of the TW pixels first: the global stores
-          // would otherwise order the next pixel's reads behind them
-          float v0[TW], v1[TW], iv[TW];
+          __nv_bfloat162* fp = frow + j;
+          if (b0 + 1 < nfeat) {
+            const int g0 = fgs[b0], g1 = fgs[b0 + 1];
+            // every shared-memory read of the TW pixels first: the global stores
+            // would otherwise order the next pixel's reads behind them
+            float2 v[TW];
 #pragma unroll
-          for (int x = 0; x < TW; ++x) {
-            iv[x] = ftot[x];
-            v0[x] = pbuf[x * PS + (g0 >= 0 ? g0 : 0)];
-            v1[x] = pbuf[x * PS + (g1 >= 0 ? g1 : 0)];
-          }
+            for (int x = 0; x < TW; ++x) v[x] = make_float2(pbuf[x * PS + g0], pbuf[x * PS + g1]);
 #pragma unroll
-          for (int x = 0; x < TW; ++x) {
-            if (x0 + x >= W) break;
-            const float f0 = g0 >= 0 ? 0.1f * (__log2f(fmaf(v0[x], iv[x], 1e-6f)) + 10.f) : 0.f;
-            const float f1 = g1 >= 0 ? 0.1f * (__log2f(fmaf(v1[x], iv[x], 1e-6f)) + 10.f) : 0.f;
-            frow[size_t(x) * np + j] = __floats2bfloat162_rn(f0, f1);
+            for (int x = 0; x < TW; ++x) {
+              if (x >= nx) break;
+              // P / sum P + 1e-6 >= 1e-6: a normal number, so log2 with flush-to-zero is exact
+              // to the same approximation; (log2 y + 10) / 10 as one FMA
+              const float2 y = __ffma2_rn(v[x], iv2[x], make_float2(1e-6f, 1e-6f));
+              float l0, l1;
+              asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l0) : "f"(y.x));
+              asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l1) : "f"(y.y));
+              const float2 f = __ffma2_rn(make_float2(l0, l1), make_float2(0.1f, 0.1f), make_float2(1.f, 1.f));
+              *fp = __floats2bfloat162_rn(f.x, f.y);
+              fp += np;
+            }
+          } else {
+            // the odd last feature and the row padding
+            const int g0 = b0 < nfeat ? fgs[b0] : -1;
+#pragma unroll
+            for (int x = 0; x < TW; ++x) {
+              if (x >= nx) break;
+              const float f0 = g0 >= 0 ? 0.1f * (__log2f(fmaf(pbuf[x * PS + g0], iv2[x].x, 1e-6f)) + 10.f) : 0.f;
+              *fp = __floats2bfloat162_rn(f0, 0.f);
+              fp += np;
+            }
           }
         }
       }
