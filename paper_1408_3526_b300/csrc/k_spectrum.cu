@@ -35,7 +35,11 @@
 //      offsets of the power block (+-h plus constants, no index table), the
 //      smoother update and the store; the next row's smoother state is
 //      prefetched with cp.async.
-// Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1), box sums(i+1)}.
+// Two barriers per row: {C(i), A(i+1)} then {D(i), B(i+1), box sums(i+1)}.  With
+// the learned estimator's features on, phase C also leaves each channel's power
+// sum, the observer warp turns them into the pixels' totals at the start of the
+// second phase, and the feature threads wait for those (a named barrier) only
+// after their reduction tasks.
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -168,8 +172,8 @@ struct SG {
   // learned-estimator features (used only when they are requested)
   static constexpr int NBINS = M * M * MZ;
   static constexpr size_t O_FGS = al16(O_OFFS + 8ull * NPL);                   // int   [NBINS] gather
-  static constexpr size_t O_FPART = al16(O_FGS + 4ull * NBINS);                // float [TW][NH1]
-  static constexpr size_t O_FTOT = al16(O_FPART + 4ull * TW * NH1);            // float [TW] 1/sum P
+  static constexpr size_t O_FCH = al16(O_FGS + 4ull * NBINS);                  // float [TW][NCHY]
+  static constexpr size_t O_FTOT = al16(O_FCH + 4ull * TW * NCHY);             // float [TW] 1/sum P
   static constexpr size_t SMEM = al16(O_FTOT + 4ull * TW);
   static_assert(RW <= 32, "the observer warp covers the row segment");
   static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
@@ -286,9 +290,9 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + G::O_MBAR);
   float2* offs = reinterpret_cast<float2*>(smem_raw + G::O_OFFS);
   int* fgs = reinterpret_cast<int*>(smem_raw + G::O_FGS);
-  float* fpart = reinterpret_cast<float*>(smem_raw + G::O_FPART);
+  float* fch = reinterpret_cast<float*>(smem_raw + G::O_FCH);
   float* ftot = reinterpret_cast<float*>(smem_raw + G::O_FTOT);
-  const bool feat = MODE != 0 && a.feat != nullptr;
+  const bool feat = MODE != 0 && !F64 && a.feat != nullptr;
   if (feat)
     for (int i = tid; i < a.feat_n; i += NTHR) fgs[i] = a.feat_gather[i];
 
@@ -609,6 +613,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       const float2 D = dbuf[(i & 1) * DC_SLOT + plc * TW + xy];
       float* pb = pbuf + xy * PS + cy * M;
       const float2 two2 = make_float2(2.f, 2.f);
+      float2 psum = make_float2(0.f, 0.f);   // features: this channel's power summed over ky
       auto dump = [&](int k, float zx, float zy, float pw) {
         // uncentred S'' = e^{+j2pi (kx+ky)K/M} Z, and its conjugate partner at -k
         if (!(DUMP && x0 + xy < W)) return;
@@ -638,6 +643,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         const float2 pw = __ffma2_rn(zr, zr, __fmul2_rn(zi, zi));
         pb[p] = pw.x;
         pb[p + K + 1] = pw.y;
+        if constexpr (MODE != 0) psum = __fadd2_rn(psum, pw);
         dump(p, zr.x, zi.x, pw.x);
         dump(p + K + 1, zr.y, zi.y, pw.y);
       }
@@ -648,6 +654,14 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       const float pwc = fmaf(zcx, zcx, zcy * zcy);
       pb[K] = pwc;
       dump(K, zcx, zcy, pwc);
+      if (feat) {
+        // every bin of a complex plane, and of a real plane's kx > 0 channel,
+        // stands for itself and its mirror -k (not stored); a real plane's
+        // kx = 0 channel holds both ky and -ky
+        const bool self_mirror = (plc == 0 || (EVEN && plc == NPL - 1)) && kxc == 0;
+        const float sc = psum.x + psum.y + pwc;
+        fch[xy * NCHY + cy] = self_mirror ? sc : 2.f * sc;
+      }
       }
     };
     auto doD = [&](int i) {               // reduce over kz, smooth (in place in the row ring)
@@ -663,22 +677,17 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         // offsets x*PS + (c*M + ky + K) with c the channel of (plane, +-hx)
         const int op = x * PS + hi + K, om = x * PS - hi + K;
         const float p0 = pbuf[op];
-        float Ac = p0, As = 0.f, ps = p0;
+        float Ac = p0, As = 0.f;
 #pragma unroll
         for (int j = 1; j <= J; ++j) {
           const float pp = pbuf[op + (G::base(j) + K) * M], pm = pbuf[om + (G::base(j) + K) * M];
           Ac = fmaf(pp + pm, c_cz[ZI][j], Ac);
           As = fmaf(pp - pm, c_sz[ZI][j], As);
-          ps += pp + pm;
         }
         if (EVEN) {
           const float pn = pbuf[op + G::base(NPL - 1) * M];
           Ac -= pn;
-          ps += pn;
         }
-        // features: this h's share of the pixel's power sum over all M^2 Mz bins
-        // (the bins at -h repeat the same values, except for h = 0)
-        if (feat) fpart[x * NH1 + hi] = hi > 0 ? 2.f * ps : ps;
         float* sp = st + x * KPAD + hi;
         sp[0] = fmaf(oma, Ac, alpha * sp[0]);
         if (hi > 0) sp[NH] = fmaf(oma, As, alpha * sp[NH]);
@@ -697,16 +706,8 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
       // block at most 2-way bank-conflicted), and a thread's two gather offsets
       // serve all TW pixels of the row.
       if (feat) {
-        constexpr int NDW = NTW / 32;
-        asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");   // all partial sums of the row
-        for (int x = tid >> 5; x < TW; x += NDW) {
-          float t = 0.f;
-          for (int h = lane; h < NH1; h += 32) t += fpart[x * NH1 + h];
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-          if (lane == 0) ftot[x] = t > 0.f ? 1.f / t : 0.f;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(NTW) : "memory");
+        // the observer warp's 1 / sum P of the row's pixels (doT)
+        asm volatile("bar.sync 1, %0;" ::"r"(NTHR) : "memory");
         const int np = a.feat_ld / 2, nfeat = a.feat_n;
         const int nx = W - x0 < TW ? W - x0 : TW;
         __nv_bfloat162* frow = reinterpret_cast<__nv_bfloat162*>(a.feat) + (size_t(yo) * W + x0) * np;
@@ -748,6 +749,35 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
             }
           }
         }
+      }
+    };
+
+    // observer warp, learned-estimator features only: 1 / (sum of P over all M^2 Mz
+    // bins) of every pixel of output row i from the y-SDFT threads' channel sums
+    // (fixed order), released to the feature threads by a named barrier that
+    // they wait on after their reduction tasks (both sides take it once per
+    // output row under the same condition)
+    auto doT = [&](int i) {
+      if constexpr (MODE != 0 && !F64) {
+        const int yo = y0 + i - 2 * K;
+        if (!(feat && i >= 2 * K && yo < y1)) return;
+        // LP lanes per pixel (a power of two), each summing every LP-th channel
+        constexpr int LP = 32 / TW >= 16 ? 16 : (32 / TW >= 8 ? 8 : (32 / TW >= 4 ? 4 : (32 / TW >= 2 ? 2 : 1)));
+        constexpr int PPASS = 32 / LP;
+#pragma unroll
+        for (int x0p = 0; x0p < TW; x0p += PPASS) {
+          const int x = x0p + lane / LP, q = lane % LP;
+          float t = 0.f;
+          if (x < TW) {
+#pragma unroll
+            for (int c = q; c < NCHY; c += LP) t += fch[x * NCHY + c];
+          }
+#pragma unroll
+          for (int off = 1; off < LP; off <<= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+          if (x < TW && q == 0) ftot[x] = t > 0.f ? 1.f / t : 0.f;
+        }
+        __syncwarp();
+        asm volatile("bar.arrive 1, %0;" ::"r"(NTHR) : "memory");
       }
     };
 
@@ -851,6 +881,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         if (i + 2 < nrows) loadA(i + 2);
       }
       __syncthreads();
+      if (owarp) doT(i);
       doD(i);
       if (i + 1 < nrows) {
         doB(i + 1);
