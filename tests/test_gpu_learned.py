@@ -106,12 +106,16 @@ def _unique_bins(M, Mz):
     return np.array(out)
 
 
+@pytest.mark.parametrize("M,Mz", [(9, 4), (15, 6), (15, 4)])
 @pytest.mark.parametrize("mode", [1, 2], ids=["all_bins", "one_per_mirror_pair"])
-def test_features_match_oracle_power(mode):
+def test_features_match_oracle_power(mode, M, Mz):
+    """Features of every bin (mode 1) or of one bin per mirror pair (mode 2)
+    against the oracle's power, for window/order shapes whose per-pixel power
+    totals are summed by one, four and two lanes per pixel."""
     import torch
 
     from paper_1408_3526_b300.stream import WhitenStream
-    M, Mz, T, H, W = 9, 4, 8, 24, 30
+    T, H, W = 8, 24, 30
     sc = scenes.small_scene(T=T, H=H, W=W, seed=8, tex_size=128)
     with WhitenStream(H, W, M, Mz, 2.0, 0.25) as s:
         assert s.lib.wh_stream_set_features(s._s, mode) == 0
