@@ -7,7 +7,9 @@ GPU path differs by:
   - FP32 accumulation of every tensor-core product (bounded by K 2^-22 of the
     sum of |terms|, four times the round-to-nearest unit roundoff, since the
     accumulation order and alignment are the hardware's);
-  - FP32 bias adds and GELU (tanhf) evaluation;
+  - FP32 bias adds and GELU evaluation (as z / (1 + e^{-2u}), the exact
+    identity for the tanh form, with the hardware exponential and a fast
+    divide: a few FP32 ulps, inside the 4 unit roundoffs allowed below);
   - BF16 rounding (unit roundoff 2^-8) of the hidden activations H1, H2, of
     the output gradient dY and of the pre-activation gradients dZ2, dZ1.
 Each error is propagated through the next product with absolute values
