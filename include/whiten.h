@@ -466,9 +466,10 @@ int wh_read_features(wh_stream *s, void *out, int is_device, int *ld);
  * takes the network's velocity rounded to the grid, every other pixel runs
  * the exact autocorrelation search.  mlp = NULL returns to the plain mode.
  * The network's forward runs on the stream's own CUDA stream (its search
- * stream with the frame pipeline).  Its activation buffers are shared, so one
- * network serves one stream at a time: streams pushing concurrently from
- * different CUDA streams need a network each. */
+ * stream with the frame pipeline).  Its activation and output buffers are
+ * shared (the selection reads the output rows in place), so one network
+ * serves one stream at a time: streams pushing concurrently from different
+ * CUDA streams need a network each. */
 int wh_stream_set_learned(wh_stream *s, wh_mlp *mlp, float conf_threshold);
 /* Frames processed in learned mode and pixel-frames sent to the search. */
 int wh_stream_learned_stats(wh_stream *s, long long *frames, long long *fallback_pixels);

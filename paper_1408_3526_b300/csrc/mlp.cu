@@ -242,6 +242,13 @@ int forward_impl(wh_mlp* m, const void* x, int ldx, int n, bool train) {
 namespace wh {
 int mlp_n_in(const wh_mlp* m) { return m ? m->n_in : 0; }
 
+// The last forward pass's outputs in the network's own buffer: [n][ld] FP32,
+// columns 0..n_out-1 used; valid until the next pass on this network.
+const float* mlp_output(const wh_mlp* m, int* ld) {
+  if (ld) *ld = m ? m->o_pad : 0;
+  return m ? m->Y : nullptr;
+}
+
 // Forward pass enqueued on `st` (the caller's stream) instead of the network's
 // own: the whitening stream's learned search runs it between its spectrum and
 // selection kernels, which must see its input and output in stream order.

@@ -133,13 +133,15 @@ static void build_spec_tables(const wh_stream* s, SpecTables& tb, std::vector<in
 
 // Learned mode: MLP velocity where its confidence passes the threshold (rounded
 // to the grid), the exact autocorrelation search for every other pixel.
-__global__ void learned_select_kernel(const float* y, int npix, float thr, float vmax, float vstep, int L,
-                                      int* vidx, float* vx, float* vy, int* list, int* nlist) {
+// y: the network's output rows (vx, vy, confidence logit) with row pitch ldy.
+__global__ void learned_select_kernel(const float* y, int ldy, int npix, float thr, float vmax, float vstep,
+                                      int L, int* vidx, float* vx, float* vy, int* list, int* nlist) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    const float c = y[3 * p + 2];
+    const float* yp = y + size_t(p) * ldy;
+    const float c = yp[2];
     const float conf = 1.f / (1.f + __expf(-c));
     if (conf >= thr) {
-      int ix = __float2int_rn((y[3 * p] + vmax) / vstep), iy = __float2int_rn((y[3 * p + 1] + vmax) / vstep);
+      int ix = __float2int_rn((yp[0] + vmax) / vstep), iy = __float2int_rn((yp[1] + vmax) / vstep);
       ix = ix < 0 ? 0 : (ix >= L ? L - 1 : ix);
       iy = iy < 0 ? 0 : (iy >= L ? L - 1 : iy);
       vidx[p] = iy * L + ix;
@@ -156,16 +158,20 @@ __global__ void accumulate_count_kernel(const int* n, long long* total) { *total
 namespace wh {
 int mlp_forward_on(wh_mlp* m, const void* x, int ldx, int n, float* y, int ldy, cudaStream_t st);
 int mlp_n_in(const wh_mlp* m);
+const float* mlp_output(const wh_mlp* m, int* ld);
 }
 
 static int learned_search(wh_stream* s) {
   const int npix = s->H * s->W;
   // on the search's stream: the network reads the features this frame's
   // spectrum kernel wrote and the selection below reads its output
-  int rc = wh::mlp_forward_on(s->mlp, s->d_feat, s->feat_ld, npix, s->d_ymlp, 3, s->st);
+  // (read in place from the network's padded output rows, no copy)
+  int rc = wh::mlp_forward_on(s->mlp, s->d_feat, s->feat_ld, npix, nullptr, 0, s->st);
   if (rc != WH_OK) return rc;
+  int ldy = 0;
+  const float* y = wh::mlp_output(s->mlp, &ldy);
   WH_CU(cudaMemsetAsync(s->d_nlist, 0, sizeof(int), s->st));
-  learned_select_kernel<<<148 * 8, 256, 0, s->st>>>(s->d_ymlp, npix, s->conf_thr, float(s->vmax),
+  learned_select_kernel<<<148 * 8, 256, 0, s->st>>>(y, ldy, npix, s->conf_thr, float(s->vmax),
                                                     float(s->vstep), s->L, s->vidx, s->vx, s->vy,
                                                     s->d_list, s->d_nlist);
   WH_CU(cudaGetLastError());
@@ -229,7 +235,7 @@ static void free_stream(wh_stream* s) {
   void* ptrs[] = {s->obs[0], s->obs[1], s->Astate, s->frame, s->whitened, s->vx, s->vy, s->vidx,
                   s->d_spec, s->d_hgather, s->d_taby, s->d_tabx, s->d_hw, s->d_dump_win,
                   s->d_dump_pow, s->d_raw, s->d_rs, s->d_a16, s->d_l1, s->d_cval, s->d_cidx,
-                  s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather, s->d_ymlp,
+                  s->d_table, s->d_err, s->d_nfb, s->d_feat, s->d_fgather,
                   s->d_list, s->d_nlist, s->d_nfb_total, s->d_det, s->d_det_list, s->d_bop,
                   s->d_tcd_table, s->d_ccount, s->d_cand, s->d_tcd_counts};
   for (void* p : ptrs)
@@ -296,7 +302,7 @@ int wh_create_stream(int H, int W, int M, int Mz, wh_vgrid grid, const wh_params
   s->d_table = nullptr; s->d_err = nullptr; s->d_nfb = nullptr;
   s->d_feat = nullptr; s->feat_ld = 0; s->feat_n = 0; s->feat_mode = 0; s->d_fgather = nullptr; s->mlp = nullptr;
   s->conf_thr = 0.8f;
-  s->d_ymlp = nullptr; s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
+  s->d_list = nullptr; s->d_nlist = nullptr; s->d_nfb_total = nullptr;
   s->mlp_frames = 0;
   s->as = nullptr;
   s->d_det = nullptr; s->det_bytes = 0; s->d_det_list = nullptr; s->det_list_cap = 0;
@@ -1009,8 +1015,7 @@ int wh_stream_set_learned(wh_stream* s, wh_mlp* mlp, float conf_threshold) {
   if (rc != WH_OK) return rc;
   const size_t npix = size_t(s->H) * s->W;
   cudaError_t e = cudaSuccess;
-  if (!s->d_ymlp) e = cudaMalloc((void**)&s->d_ymlp, sizeof(float) * 3 * npix);
-  if (e == cudaSuccess && !s->d_list) e = cudaMalloc((void**)&s->d_list, sizeof(int) * npix);
+  if (!s->d_list) e = cudaMalloc((void**)&s->d_list, sizeof(int) * npix);
   if (e == cudaSuccess && !s->d_nlist) e = cudaMalloc((void**)&s->d_nlist, sizeof(int));
   if (e == cudaSuccess && !s->d_nfb_total) {
     e = cudaMalloc((void**)&s->d_nfb_total, sizeof(long long));

@@ -59,7 +59,6 @@ struct wh_stream {
   int* d_fgather;        // [feat_n]
   struct wh_mlp* mlp;    // not owned
   float conf_thr;
-  float* d_ymlp;         // [H*W][3]
   int* d_list;           // [H*W] pixels sent to the exact search
   int* d_nlist;          // [1]
   long long* d_nfb_total;// fallback pixels accumulated
