@@ -70,6 +70,9 @@ constexpr int kSegRows = 256;       // longest run of the y-recursion (output ro
 constexpr int kMaxK = (kMaxM - 1) / 2;
 __constant__ float2 c_rwx[7][kMaxK], c_rwy[7][kMaxK], c_rnwy[7][kMaxK];
 __constant__ float2 c_rcx[7][kMaxK], c_rcy[7][kMaxK], c_rncy[7][kMaxK];
+// x-DFT weights Hann(mx) e^{j2pi kx (mx-K)/M}, kx = 0..K, per window size, as
+// (wr, wr) and (wi, wi) pairs for the packed sums over a complex row (FP32 form)
+__constant__ float2 c_xrr[7][kMaxK + 1][kMaxM], c_xii[7][kMaxK + 1][kMaxM];
 __constant__ double2 c_dw[7][kMaxM], c_dc[7][kMaxM];   // the same twiddles in double (index ky + K)
 __constant__ float2 c_lam[kZN][kMaxPlanes];
 __constant__ float2 c_hz[kZN];
@@ -127,31 +130,53 @@ struct SG {
   static constexpr int NTHR = cdiv(NCT, 32) * 32 + 32;    // + the observer warp
   static constexpr int PS = pick_pstride(TW, NCT, M, NCHY * M);   // pixel stride of pbuf
   static constexpr int KPAD = (M * M + 3) & ~3;
-  // x-DFT units (group, kx, x), group 0 = the real planes, j = complex plane j;
-  // each group padded to whole warps so a warp runs one code path
+  // x-DFT, precision form: units (group, kx, x), group 0 = the real planes,
+  // j = complex plane j; each group padded to whole warps so a warp runs one
+  // code path
   static constexpr int GU = TW * (K + 1);
   static constexpr int GP = cdiv(GU, 32) * 32;
-  static constexpr int NBT = (J + 1) * GP;                // x-DFT threads
+  // x-DFT, FP32: one lane per (slot, column), slot 0 = both real planes as one
+  // complex row (v0, v_Mz/2), slot j = complex plane j, so every lane runs the
+  // same sums; the K+1 values kx >= 0 split into NXC chunks of KC, one chunk
+  // per warp (WPC warps when the units exceed a warp), so the weights are
+  // compile-time constant-bank operands and each tap loaded once serves KC kx
+  static constexpr int XG = J + 1;
+  static constexpr int XU = XG * TW;
+  static constexpr int WPC = cdiv(XU, 32);
   static constexpr int NDT = TW * NH1;                    // reduction tasks per row
   // Reduction tasks: RD rounds on each thread without x-DFT work and RB rounds
-  // on each x-DFT thread, chosen for the shortest estimated critical path
-  // (x-DFT unit ~5.5 instr/tap, task ~25); never on the observer warp, which
-  // runs the box sums meanwhile.
+  // on each x-DFT thread, with the x-DFT split (NXC) and RB chosen for the
+  // shortest estimated critical path (instructions: x-DFT ~5.5 per tap and unit
+  // in the precision form, M loads + KC (2M + 8) + 8 per FP32 x-DFT lane,
+  // reduction task ~25); never on the observer warp, which runs the box sums
+  // meanwhile.
   static constexpr int NTW = NTHR - 32;                   // threads other than the observer warp
-  static constexpr int NOB = NTW - NBT;                   // threads without x-DFT work
-  static constexpr int BCOST = 11 * M / 2 + 12, DCOST = 25;
-  static constexpr int rd_for(int rb) {
-    return NOB > 0 ? cdiv(imax(0, NDT - NBT * rb), NOB) : (NBT * rb >= NDT ? 0 : (1 << 20));
+  static constexpr int DCOST = 25;
+  static constexpr int nbt_of(int nxc) { return F64 ? (J + 1) * GP : nxc * WPC * 32; }
+  static constexpr int bcost_of(int nxc) { return F64 ? 11 * M / 2 + 12 : M + cdiv(K + 1, nxc) * (2 * M + 8) + 8; }
+  static constexpr int rd_for(int nxc, int rb) {
+    return NTW - nbt_of(nxc) > 0 ? cdiv(imax(0, NDT - nbt_of(nxc) * rb), NTW - nbt_of(nxc))
+                                 : (nbt_of(nxc) * rb >= NDT ? 0 : (1 << 20));
   }
-  static constexpr int cost_for(int rb) { return imax(BCOST + rb * DCOST, rd_for(rb) * DCOST); }
-  static constexpr int pick_rb() {
-    int best = 0;
-    for (int rb = 1; rb <= 16; ++rb)
-      if (cost_for(rb) < cost_for(best)) best = rb;
+  static constexpr int cost_for(int nxc, int rb) {
+    return imax(bcost_of(nxc) + rb * DCOST, rd_for(nxc, rb) * DCOST);
+  }
+  // best (NXC, RB) packed as NXC * 64 + RB; NXC = 1 in the precision form
+  static constexpr int pick_split() {
+    int best = -1, bc = 1 << 30;
+    for (int nxc = 1; nxc <= (F64 ? 1 : K + 1); nxc *= 2) {
+      if (nbt_of(nxc) > NTW) break;
+      for (int rb = 0; rb <= 16; ++rb)
+        if (cost_for(nxc, rb) < bc) { bc = cost_for(nxc, rb); best = nxc * 64 + rb; }
+    }
     return best;
   }
-  static constexpr int RB = pick_rb();
-  static constexpr int RD = rd_for(RB);
+  static constexpr int NXC = pick_split() / 64;
+  static constexpr int KC = cdiv(K + 1, NXC);
+  static constexpr int NBT = nbt_of(NXC);                 // x-DFT threads
+  static constexpr int NOB = NTW - NBT;                   // threads without x-DFT work
+  static constexpr int RB = pick_split() % 64;
+  static constexpr int RD = rd_for(NXC, RB);
   static constexpr int SROW = TW * KPAD;                  // smoothed state of one output row segment
   // first channel of plane p (channel order: plane 0 kx = 0..K, complex planes
   // kx = -K..K, Nyquist plane kx = 0..K)
@@ -177,6 +202,7 @@ struct SG {
   static constexpr size_t SMEM = al16(O_FTOT + 4ull * TW);
   static_assert(RW <= 32, "the observer warp covers the row segment");
   static_assert(NBT <= NTW, "one x-DFT unit per thread, none on the observer warp");
+  static_assert(F64 || (NXC <= 8 && NXC * KC >= K + 1), "x-DFT chunks cover kx = 0..K");
   static_assert(NBT * RB + NOB * RD >= NDT, "every reduction task has a thread");
 };
 
@@ -257,6 +283,46 @@ __device__ __forceinline__ void observer_hann(const float* pa, float2 (&T)[SG<M,
   }
 }
 
+// FP32 x-DFT of one lane's (slot bg, column bx) for the kx of chunk CH: direct
+// M-tap sums over the complex row (row[-mx], mx = 0..M-1) with the weights as
+// constant-bank operands, each tap loaded once for the chunk's kx.  Slot 0
+// holds the two real planes as (v0, v_Mz/2), whose spectra are (ac.x, db.x)
+// and (ac.y, db.y); a complex plane's +kx and -kx outputs come from the same
+// accumulators (the -kx weights are the conjugates).
+template <int M, int MZ, int CH>
+__device__ __forceinline__ void xdft_chunk(const float2* __restrict__ row, float2* __restrict__ rs, int bg, int bx) {
+  using G = SG<M, MZ>;
+  constexpr int K = G::K, TW = G::TW, NPL = G::NPL, KC = G::KC, MI = (M - 3) / 2;
+  constexpr int KX0 = CH * KC;
+  constexpr int NK = KX0 >= K + 1 ? 0 : (KX0 + KC <= K + 1 ? KC : K + 1 - KX0);
+  if constexpr (NK > 0) {
+    float2 ac[NK], db[NK];   // (sum wr vr, sum wr vi), (sum wi vr, sum wi vi)
+#pragma unroll
+    for (int c = 0; c < NK; ++c) { ac[c] = make_float2(0.f, 0.f); db[c] = make_float2(0.f, 0.f); }
+#pragma unroll
+    for (int mx = 0; mx < M; ++mx) {
+      const float2 v = row[-mx];
+#pragma unroll
+      for (int c = 0; c < NK; ++c) {
+        ac[c] = __ffma2_rn(c_xrr[MI][KX0 + c][mx], v, ac[c]);
+        db[c] = __ffma2_rn(c_xii[MI][KX0 + c][mx], v, db[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NK; ++c) {
+      const int kx = KX0 + c;
+      if (bg == 0) {
+        rs[kx * TW + bx] = make_float2(ac[c].x, db[c].x);                                   // channel (0, kx)
+        if (G::EVEN) rs[(G::base(NPL - 1) + kx) * TW + bx] = make_float2(ac[c].y, db[c].y);  // (Mz/2, kx)
+      } else {
+        const int c0 = G::base(bg) + K;                                                       // channel (bg, 0)
+        rs[(c0 + kx) * TW + bx] = make_float2(ac[c].x - db[c].y, ac[c].y + db[c].x);
+        if (kx > 0) rs[(c0 - kx) * TW + bx] = make_float2(ac[c].x + db[c].y, ac[c].y - db[c].x);
+      }
+    }
+  }
+}
+
 // MODE 0: the plain path (no dump, no features, both compiled out); 1: debug
 // dump of the windowed spectrum and power (features if requested); 2: the
 // learned estimator's features.  F64: the precision form, spatial sums in
@@ -300,17 +366,13 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
   // the x-DFT weights and box sums (everything before the power is linear).
   const float sig = sqrtf(float(MZ) / float(16 * M * M));
   const double sigd = sqrt(double(MZ) / double(16 * M * M));
-  for (int i = tid; i < (K + 1) * M; i += NTHR) {
-    if constexpr (F64) {   // Hann(mx) e^{j2pi kx (mx-K)/M} sig, in double
+  if constexpr (F64) {   // Hann(mx) e^{j2pi kx (mx-K)/M} sig, in double (FP32: constant bank, sig on the rows)
+    for (int i = tid; i < (K + 1) * M; i += NTHR) {
       const int kx = i / M, mx = i % M;
       const double hann = 0.5 + 0.5 * cospi(2.0 * (mx - K) / M);
       double sn, cs;
       sincospi(2.0 * kx * (mx - K) / M, &sn, &cs);
       xw[i] = make_double2(hann * cs * sigd, hann * sn * sigd);
-    } else {
-      const float2 w = cscale(a.tables->xcoef[i / M][i % M], sig);
-      xw[i] = w;                                   // (wr, wi)
-      xw4[i] = make_float4(w.x, w.x, w.y, w.y);    // (wr, wr, wi, wi)
     }
   }
   const float alpha = a.alpha, oma = 1.0f - alpha;
@@ -328,10 +390,23 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
   else if (cy < K + 1 + J * M) { plc = 1 + (cy - (K + 1)) / M; kxc = (cy - (K + 1)) % M - K; }
   else { plc = NPL - 1; kxc = cy - (K + 1) - J * M; }
   const float wxh = kxc == 0 ? 0.5f : ((kxc == 1 || kxc == -1) ? 0.25f : 0.f);
-  // B: x-DFT unit (group bg, kx bkx, column bx)
-  const int bg = tid / G::GP, br = tid % G::GP;
-  const bool bthr = tid < G::NBT && br < G::GU;
-  const int bkx = br / TW, bx = br % TW;
+  // B: x-DFT unit.  Precision form: (group bg, kx bkx, column bx); FP32:
+  // (slot bg, column bx) for the kx of chunk bch (one chunk per warp)
+  int bg, bkx = 0, bx, bch = 0;
+  bool bthr;
+  if constexpr (F64) {
+    const int br = tid % G::GP;
+    bg = tid / G::GP;
+    bthr = tid < NBT && br < G::GU;
+    bkx = br / TW;
+    bx = br % TW;
+  } else {
+    const int wq = tid >> 5, u = (wq % G::WPC) * 32 + lane;
+    bch = wq / G::WPC;
+    bthr = tid < NBT && u < G::XU;
+    bg = bthr ? u / TW : 0;
+    bx = bthr ? u % TW : 0;
+  }
   // A: observer lane ua of the last warp
   const bool owarp = tid >= NTHR - 32;
   const int ua = lane;
@@ -424,16 +499,19 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         }
         if (EVEN) a.obs_new[(MZ - 1) * plane + o] = T[NPL - 1].x;
       }
+      if constexpr (F64) {
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) {
-        const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        if constexpr (F64) {   // exact difference in double
+        for (int p = 0; p < NPL; ++p) {   // exact difference in double, real planes as (v, v)
+          const bool real = (p == 0) || (EVEN && p == NPL - 1);
           const double vx = double(Tw[p].x) - double(offs[p].x), vy = double(Tw[p].y) - double(offs[p].y);
           twr[p * RW + ua] = real ? make_double2(vx, vx) : make_double2(vx, vy);
-        } else {
-          const float2 v = csub(Tw[p], offs[p]);
-          twr[p * RW + ua] = real ? make_float2(v.x, v.x) : v;   // real planes as (v, v)
         }
+      } else {
+        // scaled by sig; slot 0 = the real planes as one complex row (v0, v_Mz/2), slot j = plane j
+        const float vn = EVEN ? Tw[NPL - 1].x - offs[NPL - 1].x : 0.f;
+        twr[ua] = make_float2((Tw[0].x - offs[0].x) * sig, vn * sig);
+#pragma unroll
+        for (int j = 1; j <= J; ++j) twr[j * RW + ua] = cscale(csub(Tw[j], offs[j]), sig);
       }
     };
     // whole observer warp: box sums along x of input row i (the (0,0) bin of
@@ -441,14 +519,30 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
     // a ring of the last M+1 rows' sums
     auto doA2 = [&](int i) {
       C2 bs[NPL];
+      if constexpr (F64) {
 #pragma unroll
-      for (int p = 0; p < NPL; ++p) {
-        const bool real = (p == 0) || (EVEN && p == NPL - 1);
-        C2 v;
-        v.x = 0; v.y = 0;
-        if (ua < RW) v = twr[p * RW + ua];
-        bs[p].x = lane_box_sum<M>(v.x);
-        bs[p].y = real ? decltype(v.y)(0) : lane_box_sum<M>(v.y);
+        for (int p = 0; p < NPL; ++p) {
+          const bool real = (p == 0) || (EVEN && p == NPL - 1);
+          C2 v;
+          v.x = 0; v.y = 0;
+          if (ua < RW) v = twr[p * RW + ua];
+          bs[p].x = lane_box_sum<M>(v.x);
+          bs[p].y = real ? decltype(v.y)(0) : lane_box_sum<M>(v.y);
+        }
+      } else {   // slots: (plane 0, plane Mz/2), then the complex planes
+#pragma unroll
+        for (int s = 0; s <= J; ++s) {
+          float2 v = make_float2(0.f, 0.f);
+          if (ua < RW) v = twr[s * RW + ua];
+          const float bx_ = lane_box_sum<M>(v.x);
+          const float by_ = (s == 0 && !EVEN) ? 0.f : lane_box_sum<M>(v.y);
+          if (s == 0) {
+            bs[0] = make_float2(bx_, 0.f);
+            if (EVEN) bs[NPL - 1] = make_float2(by_, 0.f);
+          } else {
+            bs[s] = make_float2(bx_, by_);
+          }
+        }
       }
       if (ua < TW) {
         const int slot = i % (M + 1), oslot = (i + 1) % (M + 1);   // oslot holds row i - M
@@ -456,7 +550,8 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         const C2* dold = dbuf + ((i + 1) & 1) * DC_SLOT;
 #pragma unroll
         for (int p = 0; p < NPL; ++p) {
-          const C2 val = cscale(bs[p], F64 ? sigd : sig);
+          C2 val = bs[p];                 // FP32: the rows already carry sig
+          if constexpr (F64) val = cscale(bs[p], sigd);
           C2 run = i > 0 ? cadd(dold[p * TW + ua], val) : val;
           if (i >= M) run = csub(run, dcr[oslot * DC_SLOT + p * TW + ua]);
           dcr[slot * DC_SLOT + p * TW + ua] = val;
@@ -522,33 +617,18 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
           if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_double2(ac.x + db.y, ac.y - db.x);
         }
         return;
-      } else if (bg == 0) {               // real planes, stored (v, v): (wr, wi) x (v, v)
-        const float2* w = xw + bkx * M;
-        const float2* r0 = twr + bx + 2 * K;
-        const float2* r1 = twr + (NPL - 1) * RW + bx + 2 * K;
-        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int mx = 0; mx < M; ++mx) {
-          const float2 cw = w[mx];
-          c0 = __ffma2_rn(cw, r0[-mx], c0);
-          if (EVEN) c1 = __ffma2_rn(cw, r1[-mx], c1);
-        }
-        rs[bkx * TW + bx] = c0;                                   // channel (0, kx)
-        if (EVEN) rs[(G::base(NPL - 1) + bkx) * TW + bx] = c1;    // channel (Mz/2, kx)
-      } else {                            // complex plane bg: +kx and -kx together
-        const float4* w = xw4 + bkx * M;
+      } else {                            // FP32: this warp's kx chunk (compile-time weights)
         const float2* row = twr + bg * RW + bx + 2 * K;
-        float2 ac = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);   // (sum wr vr, sum wr vi), (sum wi vr, sum wi vi)
-#pragma unroll
-        for (int mx = 0; mx < M; ++mx) {
-          const float4 cw = w[mx];
-          const float2 v = row[-mx];
-          ac = __ffma2_rn(make_float2(cw.x, cw.y), v, ac);
-          db = __ffma2_rn(make_float2(cw.z, cw.w), v, db);
+        switch (bch) {
+          case 0: xdft_chunk<M, MZ, 0>(row, rs, bg, bx); break;
+          case 1: xdft_chunk<M, MZ, 1>(row, rs, bg, bx); break;
+          case 2: xdft_chunk<M, MZ, 2>(row, rs, bg, bx); break;
+          case 3: xdft_chunk<M, MZ, 3>(row, rs, bg, bx); break;
+          case 4: xdft_chunk<M, MZ, 4>(row, rs, bg, bx); break;
+          case 5: xdft_chunk<M, MZ, 5>(row, rs, bg, bx); break;
+          case 6: xdft_chunk<M, MZ, 6>(row, rs, bg, bx); break;
+          default: xdft_chunk<M, MZ, 7>(row, rs, bg, bx); break;
         }
-        const int c0 = G::base(bg) + K;                           // channel (bg, 0)
-        rs[(c0 + bkx) * TW + bx] = make_float2(ac.x - db.y, ac.y + db.x);
-        if (bkx > 0) rs[(c0 - bkx) * TW + bx] = make_float2(ac.x + db.y, ac.y - db.x);
       }
     };
     auto doC = [&](int i) {               // y-SDFT, Hann(ky), high-pass, power of row i
@@ -977,6 +1057,20 @@ cudaError_t spectrum_init_constants() {
       rncy[mi][p] = make_float2(-c[mi][p].y, -c[mi][q].y);
     }
   }
+  // x-DFT weights, the centred Hann-windowed DFT of Eq. (6)-(7) along x:
+  // Hann(mx) = 1/2 + 1/2 cos(2pi (mx-K)/M), phase 2pi kx (mx-K)/M
+  static float2 xrr[7][kMaxK + 1][kMaxM], xii[7][kMaxK + 1][kMaxM];
+  for (int mi = 0; mi < 7; ++mi) {
+    const int M = 2 * mi + 3, K = (M - 1) / 2;
+    for (int kx = 0; kx <= K; ++kx)
+      for (int mx = 0; mx < M; ++mx) {
+        const double hann = 0.5 + 0.5 * std::cos(2.0 * pi * (mx - K) / M);
+        const double ph = 2.0 * pi * kx * (mx - K) / M;
+        const float wr = float(hann * std::cos(ph)), wi = float(hann * std::sin(ph));
+        xrr[mi][kx][mx] = make_float2(wr, wr);
+        xii[mi][kx][mx] = make_float2(wi, wi);
+      }
+  }
   double2 dw[7][kMaxM] = {}, dc[7][kMaxM] = {};
   for (int mi = 0; mi < 7; ++mi) {
     const int M = 2 * mi + 3, K = (M - 1) / 2;
@@ -998,6 +1092,8 @@ cudaError_t spectrum_init_constants() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hz, hz, sizeof(hz));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cz, cz, sizeof(cz));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sz, sz, sizeof(sz));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_xrr, xrr, sizeof(xrr));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_xii, xii, sizeof(xii));
   if (e == cudaSuccess && dev < 64) done[dev].store(true);
   return e;
 }
