@@ -143,6 +143,56 @@ struct SG {
   static constexpr int XG = J + 1;
   static constexpr int XU = XG * TW;
   static constexpr int WPC = cdiv(XU, 32);
+  // FP32: slot stride SW of the observer rows and the lane order (unit =
+  // (lane + ROT) mod XU) picked so that the 8-byte tap loads of a half warp, and
+  // each of its ring stores, fall on distinct banks (fewest extra wavefronts)
+  static constexpr int base_of(int p) { return p == 0 ? 0 : (K + 1) + (p - 1) * M; }
+  static constexpr int spread(const int* w, int n) {   // extra wavefronts of 8-byte words w[0..n)
+    int cnt[16] = {}, mx = 0;
+    for (int i = 0; i < n; ++i) { const int b = ((w[i] % 16) + 16) % 16; if (++cnt[b] > mx) mx = cnt[b]; }
+    return mx > 0 ? mx - 1 : 0;
+  }
+  static constexpr int xdft_conflicts(int sw, int rot) {
+    int tot = 0;
+    for (int w0 = 0; w0 < WPC * 32; w0 += 16) {
+      int ld[16] = {}, r0[16] = {}, r1[16] = {}, c0[16] = {}, c1[16] = {};
+      int n = 0;
+      for (int t = w0; t < w0 + 16 && t < XU; ++t) ++n;
+      if (n == 0) break;
+      for (int kx = -1; kx <= K; ++kx) {   // kx = -1: the tap loads (weight M)
+        int nr = 0, nc = 0;
+        for (int t = w0; t < w0 + n; ++t) {
+          const int u = (t + rot) % XU, g = u / TW, bx = u % TW;
+          if (kx < 0) { ld[t - w0] = g * sw + bx; continue; }
+          if (g == 0) {
+            r0[nr] = kx * TW + bx;
+            r1[nr] = (base_of(NPL - 1) + kx) * TW + bx;
+            ++nr;
+          } else {
+            c0[nc] = (base_of(g) + K + kx) * TW + bx;
+            c1[nc] = (base_of(g) + K - kx) * TW + bx;
+            ++nc;
+          }
+        }
+        if (kx < 0) tot += M * spread(ld, n);
+        else tot += spread(r0, nr) + (EVEN ? spread(r1, nr) : 0) + spread(c0, nc) + (kx > 0 ? spread(c1, nc) : 0);
+      }
+    }
+    return tot;
+  }
+  static constexpr int pick_swrot() {   // first conflict-free pair, else the least conflicting
+    int best = RW * 64, bc = 1 << 30;
+    for (int rot = 0; rot < (XU <= 32 ? XU : 1); ++rot)
+      for (int sw = RW; sw < RW + 16; ++sw) {
+        const int c = xdft_conflicts(sw, rot);
+        if (c < bc) { bc = c; best = sw * 64 + rot; }
+        if (bc == 0) return best;
+      }
+    return best;
+  }
+  static constexpr int SWROT = F64 ? RW * 64 : pick_swrot();
+  static constexpr int SW = SWROT / 64;
+  static constexpr int ROT = SWROT % 64;
   static constexpr int NDT = TW * NH1;                    // reduction tasks per row
   // Reduction tasks: RD rounds on each thread without x-DFT work and RB rounds
   // on each x-DFT thread, with the x-DFT split (NXC) and RB chosen for the
@@ -184,7 +234,7 @@ struct SG {
   // shared-memory layout (bytes); E2 = bytes of a complex element of the sums
   static constexpr size_t E2 = F64 ? 16 : 8;
   static constexpr size_t O_TWR = 0;                                           // [NPL][RW]
-  static constexpr size_t O_RING = al16(O_TWR + E2 * NPL * RW);                // [M+1][NCHY][TW]
+  static constexpr size_t O_RING = al16(O_TWR + E2 * imax(NPL * RW, XG * SW));  // [M+1][NCHY][TW]
   static constexpr size_t O_DCR = al16(O_RING + E2 * (M + 1) * NCHY * TW);     // [M+1][NPL][TW]
   static constexpr size_t O_XW = al16(O_DCR + E2 * (M + 1) * NPL * TW);        // [K+1][M]
   static constexpr size_t O_XW4 = al16(O_XW + E2 * (K + 1) * M);               // float4 [K+1][M]
@@ -401,9 +451,10 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
     bkx = br / TW;
     bx = br % TW;
   } else {
-    const int wq = tid >> 5, u = (wq % G::WPC) * 32 + lane;
+    const int wq = tid >> 5, t = (wq % G::WPC) * 32 + lane;
+    const int u = (t + G::ROT) % G::XU;
     bch = wq / G::WPC;
-    bthr = tid < NBT && u < G::XU;
+    bthr = tid < NBT && t < G::XU;
     bg = bthr ? u / TW : 0;
     bx = bthr ? u % TW : 0;
   }
@@ -511,7 +562,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         const float vn = EVEN ? Tw[NPL - 1].x - offs[NPL - 1].x : 0.f;
         twr[ua] = make_float2((Tw[0].x - offs[0].x) * sig, vn * sig);
 #pragma unroll
-        for (int j = 1; j <= J; ++j) twr[j * RW + ua] = cscale(csub(Tw[j], offs[j]), sig);
+        for (int j = 1; j <= J; ++j) twr[j * G::SW + ua] = cscale(csub(Tw[j], offs[j]), sig);
       }
     };
     // whole observer warp: box sums along x of input row i (the (0,0) bin of
@@ -533,7 +584,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
 #pragma unroll
         for (int s = 0; s <= J; ++s) {
           float2 v = make_float2(0.f, 0.f);
-          if (ua < RW) v = twr[s * RW + ua];
+          if (ua < RW) v = twr[s * G::SW + ua];
           const float bx_ = lane_box_sum<M>(v.x);
           const float by_ = (s == 0 && !EVEN) ? 0.f : lane_box_sum<M>(v.y);
           if (s == 0) {
@@ -618,7 +669,7 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
         }
         return;
       } else {                            // FP32: this warp's kx chunk (compile-time weights)
-        const float2* row = twr + bg * RW + bx + 2 * K;
+        const float2* row = twr + bg * G::SW + bx + 2 * K;
         switch (bch) {
           case 0: xdft_chunk<M, MZ, 0>(row, rs, bg, bx); break;
           case 1: xdft_chunk<M, MZ, 1>(row, rs, bg, bx); break;
