@@ -55,7 +55,13 @@ __global__ void __launch_bounds__(kWarps4 * 32) autocorr_kernel(const AutocorrAr
   // it as soon as the Q sums of this one are built (it lands during the stages)
   float* abuf = sbase + slot * KP;                                              // [KP]
   float* qbuf = sbase + NSLOT * KP + slot * QS;                                 // [QN]
-  float2* tbuf = reinterpret_cast<float2*>(sbase + NSLOT * (KP + QS)) + slot * TS;   // [K+1][LP]
+  // T buffers in the order (group, warp), groups 2 and 3 shifted by 4 words: the
+  // two groups of a half warp then sit 4 TS 8-byte words apart, 8 (mod 16)
+  // whenever TS = 2 (mod 4) (M = 7, 11, 15, or LP = 32), so their stage-1
+  // stores of 8 consecutive words fall on complementary banks, and the four
+  // groups' 4-byte broadcast reads of T(0, row) fall on four distinct banks
+  const int tslot = grp * kWarps4 + wid;
+  float2* tbuf = reinterpret_cast<float2*>(sbase + NSLOT * (KP + QS)) + tslot * TS + ((grp & 2) ? 4 : 0);   // [K+1][LP]
   const bool act0 = j < Lh, act1 = j + kGrp < Lh;
   const int l0 = j, l1 = j + kGrp;
   float2 c0[K], c1[K];
@@ -262,7 +268,7 @@ cudaError_t launch_mp(const AutocorrArgs& a, cudaStream_t st) {
   using GE = ac::Geo<M>;
   constexpr int K = GE::K, NSLOT = kWarps4 * 4;
   const size_t smem = sizeof(float) * size_t(NSLOT) * (GE::KP + GE::QN + 4) +
-                      sizeof(float2) * size_t(NSLOT) * ((K + 1) * LP + 2);
+                      sizeof(float2) * (size_t(NSLOT) * ((K + 1) * LP + 2) + 4);
   const long long npix = (long long)a.H * a.W;   // a pixel list is at most this long
   auto kern = a.rs_out ? autocorr_kernel<M, true, LP> : autocorr_kernel<M, false, LP>;
   // all of the SM's unified L1/shared storage as shared memory: four blocks
