@@ -52,3 +52,14 @@ def test_parity_random_shape(i, M, Mz, vmax, step, H, W, vx, vy, precision):
     sc = scenes.small_scene(T=T, H=H, W=W, seed=100 + i, vx=vx, vy=vy, tex_size=128)
     _compare(sc.frames, M, Mz, vmax, step, spec_frames=(T - 1,), check_vel_frac=False,
              precision=precision)
+
+
+@pytest.mark.parametrize("M,Mz", [(M, Mz) for M in SUPPORTED for Mz in SUPPORTED[M]])
+def test_parity_every_window_and_order(M, Mz):
+    """Every compiled (window, temporal order) of the spectrum kernel against
+    the oracle on a frame of several strips with a ragged last strip: each has
+    its own compile-time tile width, x-DFT split, observer-row stride and lane
+    order (Eq. (6)-(10), Eq. (1)-(2))."""
+    T = 8
+    sc = scenes.small_scene(T=T, H=20, W=67, seed=300 + 10 * M + Mz, vx=0.6, vy=-0.4, tex_size=128)
+    _compare(sc.frames, M, Mz, 1.5, 0.5, spec_frames=(T - 1,), check_vel_frac=False)
