@@ -233,12 +233,12 @@ struct SG {
   __host__ __device__ static constexpr int base(int p) { return p == 0 ? 0 : (K + 1) + (p - 1) * M; }
   // shared-memory layout (bytes); E2 = bytes of a complex element of the sums
   static constexpr size_t E2 = F64 ? 16 : 8;
-  static constexpr size_t O_TWR = 0;                                           // [NPL][RW]
+  static constexpr size_t O_TWR = 0;                          // [NPL][RW] (precision form), [XG][SW] (FP32)
   static constexpr size_t O_RING = al16(O_TWR + E2 * imax(NPL * RW, XG * SW));  // [M+1][NCHY][TW]
   static constexpr size_t O_DCR = al16(O_RING + E2 * (M + 1) * NCHY * TW);     // [M+1][NPL][TW]
+  // x-DFT weights in double, precision form only (FP32: constant bank)
   static constexpr size_t O_XW = al16(O_DCR + E2 * (M + 1) * NPL * TW);        // [K+1][M]
-  static constexpr size_t O_XW4 = al16(O_XW + E2 * (K + 1) * M);               // float4 [K+1][M]
-  static constexpr size_t O_PBUF = al16(O_XW4 + 16ull * (K + 1) * M);          // float  [TW][PS]
+  static constexpr size_t O_PBUF = al16(O_XW + (F64 ? E2 * (K + 1) * M : 0));  // float  [TW][PS]
   static constexpr size_t O_DBUF = al16(O_PBUF + 4ull * TW * PS);              // [2][NPL][TW]
   static constexpr size_t O_ABUF = al16(O_DBUF + E2 * 2 * NPL * TW);           // float  [RW][MZ+1]
   static constexpr size_t O_SROW = al16(O_ABUF + 4ull * RW * (MZ + 1));        // float  [3][SROW]
@@ -398,7 +398,6 @@ __global__ void __launch_bounds__(SG<M, MZ, F64>::NTHR, F64 ? 1 : 2) spectrum_ke
   C2* ring = reinterpret_cast<C2*>(smem_raw + G::O_RING);
   C2* dcr = reinterpret_cast<C2*>(smem_raw + G::O_DCR);
   C2* xw = reinterpret_cast<C2*>(smem_raw + G::O_XW);
-  float4* xw4 = reinterpret_cast<float4*>(smem_raw + G::O_XW4);
   float* pbuf = reinterpret_cast<float*>(smem_raw + G::O_PBUF);
   C2* dbuf = reinterpret_cast<C2*>(smem_raw + G::O_DBUF);
   float* abuf = reinterpret_cast<float*>(smem_raw + G::O_ABUF);
